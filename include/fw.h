@@ -1,0 +1,220 @@
+/*
+ * fw.h -- C ABI of the GB300 blocked Floyd-Warshall library (libfw.so).
+ *
+ * Problem (Sec. 2.3 of Calderon, Rucci, Chichizola, "Enhanced OpenMP Algorithm
+ * to Compute All-Pairs Shortest Path on x86 Architectures"): given a dense
+ * n x n distance matrix D whose entry D[i][j] is the weight of the edge i -> j
+ * (INF when there is no edge, 0 on the diagonal), compute in place the length
+ * of the shortest i -> j path for every pair, and a matrix P that records the
+ * paths.  The blocked schedule (Sec. 2.3.1: R = ceil(n/BS) rounds of pivot
+ * block, pivot row/column blocks, remaining blocks) and the intra-round
+ * concurrency of Opt-9 (Sec. 3.2) are realised on the GPU by the kernels
+ * behind these calls; the library form itself is the paper's future-work item
+ * "a library for third-party C/C++ programs" (Sec. 5).
+ *
+ * Conventions shared by every entry point
+ *   - Matrices are row-major with leading dimension ld >= n (elements).  Rows
+ *     must start on 16-byte boundaries: the base pointer is 16-byte aligned and
+ *     ld is a multiple of 4.  Entries in columns [n, ld) are never read or
+ *     written.
+ *   - int32 path: a missing edge is FW_INF_I32 = 2^29; weights are in
+ *     [0, FW_INF_I32) and every simple path is shorter than FW_INF_I32, i.e.
+ *     (n-1) * max_weight < 2^29.  Results for unreachable pairs are exactly
+ *     FW_INF_I32.  fp32 path: a missing edge is +inf; no NaN.
+ *   - D[i][i] must be 0 on entry and weights must be >= 0; results for
+ *     negative weights are undefined, except that a negative diagonal entry
+ *     seen during the solve is reported as FW_ERR_NEG_CYCLE.
+ *   - Predecessors: pred[i][j] is the LAST HOP of the chosen shortest i -> j
+ *     path (the vertex just before j), -1 on the diagonal and for unreachable
+ *     pairs.  The paper's P stores the intermediate vertex k and compares with
+ *     ">="; this library relaxes only on a strict improvement and stores the
+ *     last hop, which makes pred independent of the blocked visiting order on
+ *     every pair whose shortest path is unique.  Where several shortest paths
+ *     exist, pred is the last hop of one of them.
+ *   - Device calls are asynchronous and stream-ordered on `stream` (a
+ *     cudaStream_t; NULL is the legacy default stream).  Argument errors are
+ *     detected on the host and returned before anything is launched.  Errors
+ *     found on the device (a dependency wait that timed out, a negative cycle)
+ *     are recorded in the status word of the stream's workspace, which
+ *     fw_sync_status reads.
+ *   - The library owns a workspace per (device, stream): tile flags, panel
+ *     snapshots and the status word.  It is allocated on first use with
+ *     cudaMalloc, grows when a larger problem arrives, and is freed by
+ *     fw_release_workspace.  Two solves in flight on the same stream share it
+ *     safely (stream order); solves on different streams use different
+ *     workspaces.  Allocation cannot happen during CUDA-graph capture: run one
+ *     solve of the largest size on the stream before capturing.
+ *   - Thread safety: every entry point may be called from several host threads
+ *     on different streams.
+ */
+#ifndef FW_GB300_H
+#define FW_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FW_INF_I32 (1 << 29)
+
+typedef enum { FW_I32 = 0, FW_F32 = 1 } fw_dtype;
+
+typedef enum {
+  FW_OK = 0,
+  FW_ERR_ARG = 1,          /* invalid argument (NULL, n <= 0, ld < n, misaligned, bad option) */
+  FW_ERR_CUDA = 2,         /* a CUDA runtime call failed */
+  FW_ERR_TIMEOUT = 3,      /* a device-side dependency wait exceeded its bound */
+  FW_ERR_NEG_CYCLE = 4,    /* some D[i][i] < 0 after the solve */
+  FW_ERR_NOMEM = 5,        /* device or pinned-host allocation failed */
+  FW_ERR_UNSUPPORTED = 6   /* dtype or size not supported by this entry point */
+} fw_status;
+
+typedef enum {
+  FW_DRIVER_AUTO = 0,       /* persistent driver */
+  FW_DRIVER_PERSISTENT = 1, /* one cooperative launch; tiles scheduled by ready flags */
+  FW_DRIVER_PHASED = 2      /* one launch per phase per round (pivot, panels, remaining) */
+} fw_driver;
+
+typedef struct fw_options {
+  int32_t bs;                 /* block size BS (Sec. 2.3.1): 0 = automatic, else 32, 64 or 128 */
+  int32_t driver;             /* fw_driver */
+  int32_t lookahead;          /* persistent driver: remaining-block tasks of round r queued
+                                 between the pivot and the panels of round r+1; -1 = automatic */
+  int32_t grid;               /* persistent driver: CTAs; 0 = every co-resident CTA */
+  int64_t timeout_ns;         /* bound on one device-side dependency wait; 0 = 2 s */
+  int32_t packed_keys;        /* int32 only: 1 (default) relaxes packed (distance, pivot) keys
+                                 when the tile bounds allow it, 0 = always the generic kernel */
+  int32_t debug_skip_release; /* >= 0: the persistent driver never publishes the completion of
+                                 this task index, so that its dependents time out; -1 = off */
+  void* ev_start;             /* optional cudaEvent_t recorded just before the solver kernels */
+  void* ev_stop;              /* optional cudaEvent_t recorded just after them */
+} fw_options;
+
+/* Fills *opt with the defaults used by fw_solve. */
+void fw_options_default(fw_options* opt);
+
+/* Human-readable name of a status code (static storage). */
+const char* fw_status_string(fw_status s);
+
+/*
+ * fw_solve: all-pairs shortest paths of one graph, in place (Sec. 2.3, the
+ * blocked algorithm of Sec. 2.3.1).
+ *   dist  device pointer, n x ld, dtype elements; holds the weights on entry
+ *         and the distances on exit.
+ *   pred  device pointer, n x ld int32, output only (may not alias dist).
+ *   n     vertices, 1 <= n <= 131072.   ld  leading dimension, ld >= n, ld % 4 == 0.
+ *   dtype FW_I32 or FW_F32.
+ * Returns FW_OK once the work is enqueued.
+ */
+fw_status fw_solve(void* dist, int32_t* pred, int64_t n, int64_t ld, fw_dtype dtype, void* stream);
+
+/* fw_solve with explicit options (opt may be NULL for the defaults). */
+fw_status fw_solve_ex(void* dist, int32_t* pred, int64_t n, int64_t ld, fw_dtype dtype,
+                      const fw_options* opt, void* stream);
+
+/*
+ * fw_solve_host: the same solve on HOST buffers.  dist_host (n x ld, dtype)
+ * is copied to the device, solved, and dist_host / pred_host (n x ld int32)
+ * receive the results.  Pinned host memory gives full copy bandwidth; pageable
+ * memory works too.  Synchronous: returns after the results are on the host,
+ * with any device-side error (as fw_sync_status would report it).  Device
+ * buffers are cached per (device, stream) like the workspace.
+ */
+fw_status fw_solve_host(void* dist_host, int32_t* pred_host, int64_t n, int64_t ld,
+                        fw_dtype dtype, const fw_options* opt, void* stream);
+
+/*
+ * Batched solve of many independent graphs of different sizes in one
+ * persistent launch (graphs interleave in one task queue; BS is chosen per
+ * size class).  The plan fixes the sizes and leading dimensions; its device
+ * tables and workspace are allocated at creation, so fw_solve_batched itself
+ * allocates nothing and can be captured into a CUDA graph.
+ *   n[b], ld[b]  vertex count and leading dimension of graph b (same rules as
+ *                fw_solve), 0 <= b < batch, 1 <= batch <= 65536.
+ *   opt->bs      0 = per-size-class choice (autotuned table), else a fixed BS.
+ */
+typedef struct fw_batched_plan fw_batched_plan;
+
+fw_status fw_batched_plan_create(fw_batched_plan** plan, const int64_t* n, const int64_t* ld,
+                                 int64_t batch, fw_dtype dtype, const fw_options* opt);
+
+/* dist[b], pred[b]: HOST arrays of device pointers (batch entries each). */
+fw_status fw_solve_batched(fw_batched_plan* plan, void* const* dist, int32_t* const* pred,
+                           void* stream);
+
+/* Block size chosen for graph b, and the total number of tasks in the queue. */
+fw_status fw_batched_plan_info(const fw_batched_plan* plan, int32_t* bs_per_graph,
+                               int64_t* total_tasks);
+
+fw_status fw_batched_plan_destroy(fw_batched_plan* plan);
+
+/*
+ * fw_backward: gradient of a scalar loss L through the fp32 distances.  Given
+ * grad_dist = dL/dD, the forward result dist and its predecessors pred, writes
+ * grad_w = dL/dW, where W is the weight matrix the forward solve received:
+ *   dL/dW[u][v] = sum over pairs (i, j) whose recorded path i -> j uses the
+ *                 edge u -> v of dL/dD[i][j].
+ * The path of (i, j) is the one recorded by pred (a subgradient where shortest
+ * paths are not unique).  grad_w is 0 on non-edges, non-tree edges and the
+ * diagonal; dL/dD on the diagonal and on unreachable pairs is ignored.  Not
+ * part of the paper; it makes the solve usable inside a training graph.
+ * All pointers are device memory, n x ld (grad_w fully overwritten on [0,n)^2).
+ */
+fw_status fw_backward(const float* grad_dist, const float* dist, const int32_t* pred,
+                      float* grad_w, int64_t n, int64_t ld, void* stream);
+
+/* fw_backward over `batch` graphs of the same n stored `stride` elements apart. */
+fw_status fw_backward_strided(const float* grad_dist, const float* dist, const int32_t* pred,
+                              float* grad_w, int64_t n, int64_t ld, int64_t batch,
+                              int64_t stride, void* stream);
+
+/*
+ * fw_sync_status: waits for `stream`, then returns and clears the sticky
+ * device-side status recorded by solves on this (device, stream) pair
+ * (FW_ERR_TIMEOUT, FW_ERR_NEG_CYCLE), or FW_ERR_CUDA when the stream reports a
+ * CUDA error.
+ */
+fw_status fw_sync_status(void* stream);
+
+/* Frees every cached workspace of the calling thread's current device. */
+fw_status fw_release_workspace(void);
+
+/*
+ * fw_peak_probe: measures the min-plus relaxation peak of this GPU at its
+ * current clocks with register-resident relaxation chains on every SM (the
+ * same instruction the solver's inner loop issues: __viaddmin for int32,
+ * add + min for fp32).  Outputs relaxations per second, relaxations per SM
+ * clock cycle (clock-independent) and the average SM clock in MHz seen by the
+ * probe.  Synchronous.  Not part of the paper: it provides the roofline.
+ */
+fw_status fw_peak_probe(fw_dtype dtype, double* relax_per_s, double* relax_per_sm_clk,
+                        double* sm_mhz, void* stream);
+
+/*
+ * fw_verify_certificate: GPU check of the LP-duality certificate of exact
+ * int32 shortest distances (the checks a correct solve must pass at any size):
+ *   bad[0] D[i][i] != 0;  bad[1] a reachable (i, j) whose pred is not a tight
+ *   last hop (D[i][p] + W[p][j] != D[i][j] or no edge p -> j);  bad[2] an edge
+ *   u -> v with D[i][v] > D[i][u] + W[u][v];  bad[3] pred set on the diagonal
+ *   or an unreachable pair, or missing on a reachable one.
+ * W, dist, pred: device, n x ld.  bad: HOST array of 4 int64.  Synchronous.
+ * It shares no code with the solver kernels.
+ */
+fw_status fw_verify_certificate(const int32_t* W, const int32_t* dist, const int32_t* pred,
+                                int64_t n, int64_t ld, int64_t* bad, void* stream);
+
+/*
+ * fw_queue_tasks: diagnostic view of the persistent driver's task queue for R
+ * tile rows (R = ceil(n / BS)) and a given lookahead (the value fw_options
+ * .lookahead resolves to).  Writes 4 int32 per task -- type (0 pivot, 1 row
+ * panel, 2 column panel, 3 remaining tile), round, tile row, tile column --
+ * for the tasks [first, first + count) of the R^3 in the queue.  Host only.
+ */
+fw_status fw_queue_tasks(int32_t R, int64_t lookahead, int64_t first, int64_t count, int32_t* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FW_GB300_H */

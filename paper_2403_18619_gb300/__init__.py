@@ -1,0 +1,237 @@
+"""Python binding of libfw.so, the GB300 blocked Floyd-Warshall library.
+
+Argument marshalling only: every step of the solve runs in the CUDA kernels of
+libfw.so (see include/fw.h for the C ABI these functions mirror).  PyTorch is
+used for device memory and streams.  There is no CPU fallback: importing the
+binding works without a GPU, but any call fails loudly when libfw.so is
+missing or no CUDA device is present.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+__all__ = [
+    "FWError", "Options", "load", "fw_solve", "fw_solve_ex", "fw_solve_host", "fw_sync_status",
+    "fw_peak_probe", "fw_verify_certificate", "fw_release_workspace", "solve", "check",
+    "INF_I32", "FW_I32", "FW_F32", "DRIVER_AUTO", "DRIVER_PERSISTENT", "DRIVER_PHASED",
+]
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfw.so")
+
+INF_I32 = 1 << 29
+FW_I32, FW_F32 = 0, 1
+DRIVER_AUTO, DRIVER_PERSISTENT, DRIVER_PHASED = 0, 1, 2
+
+STATUS = {0: "FW_OK", 1: "FW_ERR_ARG", 2: "FW_ERR_CUDA", 3: "FW_ERR_TIMEOUT",
+          4: "FW_ERR_NEG_CYCLE", 5: "FW_ERR_NOMEM", 6: "FW_ERR_UNSUPPORTED"}
+
+
+class FWError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        super().__init__("%s (%d)%s" % (STATUS.get(code, "?"), code, (": " + what) if what else ""))
+
+
+class Options(ctypes.Structure):
+    """Mirror of fw_options (include/fw.h)."""
+    _fields_ = [
+        ("bs", ctypes.c_int32),
+        ("driver", ctypes.c_int32),
+        ("lookahead", ctypes.c_int32),
+        ("grid", ctypes.c_int32),
+        ("timeout_ns", ctypes.c_int64),
+        ("packed_keys", ctypes.c_int32),
+        ("debug_skip_release", ctypes.c_int32),
+        ("ev_start", ctypes.c_void_p),
+        ("ev_stop", ctypes.c_void_p),
+    ]
+
+    @classmethod
+    def default(cls, **kw) -> "Options":
+        o = cls()
+        load().fw_options_default(ctypes.byref(o))
+        for k, v in kw.items():
+            if not hasattr(o, k):
+                raise TypeError("unknown option %r" % k)
+            setattr(o, k, v)
+        return o
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load():
+    """Load libfw.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libfw.so is not built (%s); run __graft_entry__.build() or "
+                               "python paper_2403_18619_gb300/build.py" % LIB_PATH)
+        lib = ctypes.CDLL(LIB_PATH)
+        P, I64, I32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+        lib.fw_options_default.argtypes = [P]
+        lib.fw_options_default.restype = None
+        lib.fw_status_string.argtypes = [I32]
+        lib.fw_status_string.restype = ctypes.c_char_p
+        lib.fw_solve.argtypes = [P, P, I64, I64, I32, P]
+        lib.fw_solve_ex.argtypes = [P, P, I64, I64, I32, P, P]
+        lib.fw_solve_host.argtypes = [P, P, I64, I64, I32, P, P]
+        lib.fw_batched_plan_create.argtypes = [P, P, P, I64, I32, P]
+        lib.fw_solve_batched.argtypes = [P, P, P, P]
+        lib.fw_batched_plan_info.argtypes = [P, P, P]
+        lib.fw_batched_plan_destroy.argtypes = [P]
+        lib.fw_backward.argtypes = [P, P, P, P, I64, I64, P]
+        lib.fw_backward_strided.argtypes = [P, P, P, P, I64, I64, I64, I64, P]
+        lib.fw_sync_status.argtypes = [P]
+        lib.fw_release_workspace.argtypes = []
+        lib.fw_peak_probe.argtypes = [I32, P, P, P, P]
+        lib.fw_verify_certificate.argtypes = [P, P, P, I64, I64, P, P]
+        lib.fw_queue_tasks.argtypes = [I32, I64, I64, I64, P]
+        for name in ("fw_solve", "fw_solve_ex", "fw_solve_host", "fw_batched_plan_create",
+                     "fw_solve_batched", "fw_batched_plan_info", "fw_batched_plan_destroy",
+                     "fw_backward", "fw_backward_strided", "fw_sync_status",
+                     "fw_release_workspace", "fw_peak_probe", "fw_verify_certificate",
+                     "fw_queue_tasks"):
+            getattr(lib, name).restype = I32
+        _lib = lib
+        return lib
+
+
+def check(code: int, what: str = "") -> None:
+    if code != 0:
+        raise FWError(code, what)
+
+
+# ------------------------------------------------------------- marshalling ---
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _dtype_code(t) -> int:
+    import torch
+    if t.dtype == torch.int32:
+        return FW_I32
+    if t.dtype == torch.float32:
+        return FW_F32
+    raise TypeError("dist must be int32 or float32, got %s" % t.dtype)
+
+
+def _matrix(t, name):
+    """(pointer, n, ld) of a CUDA 2-D tensor with unit column stride."""
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if t.dim() != 2 or t.shape[0] != t.shape[1] or t.stride(1) != 1:
+        raise ValueError("%s must be an n x n view with unit column stride" % name)
+    return t.data_ptr(), t.shape[0], t.stride(0)
+
+
+def fw_solve(dist, pred, stream=None) -> None:
+    """fw_solve on CUDA tensors (n x n views, leading dimension = row stride)."""
+    dp, n, ld = _matrix(dist, "dist")
+    pp, n2, ld2 = _matrix(pred, "pred")
+    if n2 != n or ld2 != ld:
+        raise ValueError("dist and pred must have the same shape and row stride")
+    check(load().fw_solve(dp, pp, n, ld, _dtype_code(dist), _stream_ptr(stream)), "fw_solve")
+
+
+def fw_solve_ex(dist, pred, options: Options | None = None, stream=None) -> None:
+    dp, n, ld = _matrix(dist, "dist")
+    pp, n2, ld2 = _matrix(pred, "pred")
+    if n2 != n or ld2 != ld:
+        raise ValueError("dist and pred must have the same shape and row stride")
+    o = ctypes.byref(options) if options is not None else None
+    check(load().fw_solve_ex(dp, pp, n, ld, _dtype_code(dist), o, _stream_ptr(stream)),
+          "fw_solve_ex")
+
+
+def fw_solve_host(dist: np.ndarray, pred: np.ndarray, options: Options | None = None,
+                  stream=None) -> None:
+    """fw_solve_host on host arrays (numpy or pinned CPU torch tensors), synchronous."""
+    import torch
+    if isinstance(dist, torch.Tensor):
+        dptr, n, ld = dist.data_ptr(), dist.shape[0], dist.stride(0)
+        code = _dtype_code(dist)
+        pptr = pred.data_ptr()
+    else:
+        if dist.ndim != 2 or dist.strides[1] != dist.itemsize:
+            raise ValueError("dist must be a 2-D array with unit column stride")
+        n, ld = dist.shape[0], dist.strides[0] // dist.itemsize
+        code = FW_I32 if dist.dtype == np.int32 else FW_F32 if dist.dtype == np.float32 else None
+        if code is None:
+            raise TypeError("dist must be int32 or float32")
+        dptr, pptr = dist.ctypes.data, pred.ctypes.data
+    o = ctypes.byref(options) if options is not None else None
+    check(load().fw_solve_host(dptr, pptr, n, ld, code, o, _stream_ptr(stream)), "fw_solve_host")
+
+
+def fw_sync_status(stream=None) -> None:
+    check(load().fw_sync_status(_stream_ptr(stream)), "device status")
+
+
+def fw_release_workspace() -> None:
+    check(load().fw_release_workspace(), "fw_release_workspace")
+
+
+def fw_peak_probe(dtype: int = FW_I32, stream=None):
+    """(relaxations/s, relaxations per SM clock, average SM MHz) at the current clocks."""
+    a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    check(load().fw_peak_probe(dtype, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
+                               _stream_ptr(stream)), "fw_peak_probe")
+    return a.value, b.value, c.value
+
+
+def fw_verify_certificate(W, dist, pred, stream=None) -> np.ndarray:
+    """GPU certificate counts [diag, tight pred, feasibility, pred domain] (int32 only)."""
+    wp, n, ld = _matrix(W, "W")
+    dp, _, _ = _matrix(dist, "dist")
+    pp, _, _ = _matrix(pred, "pred")
+    bad = np.zeros(4, np.int64)
+    check(load().fw_verify_certificate(wp, dp, pp, n, ld, bad.ctypes.data, _stream_ptr(stream)),
+          "fw_verify_certificate")
+    return bad
+
+
+def fw_queue_tasks(R: int, lookahead: int, first: int = 0, count: int | None = None) -> np.ndarray:
+    """The persistent driver's queue: rows of (type, round, tile row, tile column)."""
+    if count is None:
+        count = R ** 3 - first
+    out = np.zeros((count, 4), np.int32)
+    check(load().fw_queue_tasks(R, lookahead, first, count, out.ctypes.data), "fw_queue_tasks")
+    return out
+
+
+# ------------------------------------------------------------ convenience ---
+
+def padded(n: int) -> int:
+    """Smallest leading dimension >= n that keeps rows 16-byte aligned."""
+    return (n + 3) // 4 * 4
+
+
+def solve(W, options: Options | None = None, stream=None, sync: bool = True):
+    """Out-of-place solve of a CUDA n x n weight matrix: returns (D, P) views."""
+    import torch
+    n = W.shape[0]
+    ld = padded(n)
+    Dbuf = torch.empty((n, ld), dtype=W.dtype, device=W.device)
+    Pbuf = torch.empty((n, ld), dtype=torch.int32, device=W.device)
+    D, P = Dbuf[:, :n], Pbuf[:, :n]
+    D.copy_(W)
+    fw_solve_ex(D, P, options, stream)
+    if sync:
+        fw_sync_status(stream)
+    return D, P

@@ -1,0 +1,324 @@
+// Host side of the C ABI (include/fw.h): argument checks, workspace cache and
+// dispatch to the solver launchers.
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <utility>
+#include <vector>
+
+#include "fw_internal.h"
+
+namespace fwh {
+
+namespace {
+
+constexpr size_t kAlign = 256;
+size_t up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+struct StreamWs {
+  void* base = nullptr;
+  size_t bytes = 0;
+  int cached_R = -1, cached_BS = -1;
+  int64_t cached_look = -1;
+  // host-buffer path (fw_solve_host)
+  void* hd = nullptr;
+  void* hp = nullptr;
+  size_t hbytes = 0;
+  int* status = nullptr;  // sticky status word of this stream (lives in `sbase`)
+  void* sbase = nullptr;
+};
+
+std::mutex g_mu;
+std::map<std::pair<int, cudaStream_t>, StreamWs> g_ws;
+std::map<int, int> g_sms;
+
+}  // namespace
+
+int num_sms() {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(g_mu);
+  auto it = g_sms.find(dev);
+  if (it != g_sms.end()) return it->second;
+  int v = 0;
+  cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+  if (v <= 0) v = 1;
+  g_sms[dev] = v;
+  return v;
+}
+
+size_t solve_ws_bytes(int R, int BS) {
+  const size_t t = (size_t)BS * BS;
+  size_t b = 0;
+  b += up((size_t)R * R * 4 + 4 * 4 + 4);  // ver + ctr + abort
+  b += up((size_t)(R + 2) * 4);            // stage offsets
+  b += up(2 * t * 4) * 2;                  // piv, pivP
+  b += up(2 * (size_t)R * t * 4) * 5;      // colK, colR, rowK, rowR, rowP
+  b += up(2 * (size_t)R * 4) * 2;          // colB, rowB
+  return b + kAlign;
+}
+
+SolveWs carve_solve_ws(void* base, int R, int BS) {
+  SolveWs w;
+  char* p = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(base) + kAlign - 1) / kAlign * kAlign);
+  const size_t t = (size_t)BS * BS;
+  w.ver = reinterpret_cast<int*>(p);
+  w.ctr = reinterpret_cast<unsigned*>(w.ver + (size_t)R * R);
+  w.abort_flag = reinterpret_cast<int*>(w.ctr + 4);
+  w.flags_bytes = (size_t)R * R * 4 + 4 * 4 + 4;
+  p += up(w.flags_bytes);
+  w.stage_off = reinterpret_cast<unsigned*>(p);  p += up((size_t)(R + 2) * 4);
+  w.piv = p;                                     p += up(2 * t * 4);
+  w.pivP = reinterpret_cast<int32_t*>(p);        p += up(2 * t * 4);
+  w.colK = reinterpret_cast<uint32_t*>(p);       p += up(2 * (size_t)R * t * 4);
+  w.colR = p;                                    p += up(2 * (size_t)R * t * 4);
+  w.rowK = reinterpret_cast<uint32_t*>(p);       p += up(2 * (size_t)R * t * 4);
+  w.rowR = p;                                    p += up(2 * (size_t)R * t * 4);
+  w.rowP = reinterpret_cast<int32_t*>(p);        p += up(2 * (size_t)R * t * 4);
+  w.colB = reinterpret_cast<int32_t*>(p);        p += up(2 * (size_t)R * 4);
+  w.rowB = reinterpret_cast<int32_t*>(p);        p += up(2 * (size_t)R * 4);
+  w.R = R; w.BS = BS; w.slot_tiles = R;
+  return w;
+}
+
+int pick_bs(int64_t n) {
+  if (n <= 512) return 32;
+  if (n <= 4096) return 64;
+  return 128;
+}
+
+// Workspace for (current device, stream), grown to `need` bytes.  Caller holds g_mu.
+static fw_status get_ws(cudaStream_t s, size_t need, StreamWs** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return FW_ERR_CUDA;
+  StreamWs& w = g_ws[{dev, s}];
+  if (!w.sbase) {
+    if (cudaMalloc(&w.sbase, 256) != cudaSuccess) return FW_ERR_NOMEM;
+    if (cudaMemset(w.sbase, 0, 256) != cudaSuccess) return FW_ERR_CUDA;
+    w.status = reinterpret_cast<int*>(w.sbase);
+  }
+  if (w.bytes < need) {
+    if (w.base) {
+      cudaStreamSynchronize(s);
+      cudaFree(w.base);
+      w.base = nullptr;
+      w.bytes = 0;
+    }
+    if (cudaMalloc(&w.base, need) != cudaSuccess) {
+      cudaGetLastError();
+      return FW_ERR_NOMEM;
+    }
+    w.bytes = need;
+    w.cached_R = -1;
+  }
+  *out = &w;
+  return FW_OK;
+}
+
+fw_status check_matrix_args(const void* dist, const void* pred, int64_t n, int64_t ld) {
+  if (!dist || !pred) return FW_ERR_ARG;
+  if (n <= 0 || n > 131072 || ld < n || (ld % 4) != 0) return FW_ERR_ARG;
+  if ((reinterpret_cast<uintptr_t>(dist) & 15) || (reinterpret_cast<uintptr_t>(pred) & 15))
+    return FW_ERR_ARG;
+  if (dist == (const void*)pred) return FW_ERR_ARG;
+  return FW_OK;
+}
+
+fw_status check_options(const fw_options& o) {
+  if (o.bs != 0 && o.bs != 32 && o.bs != 64 && o.bs != 128) return FW_ERR_ARG;
+  if (o.driver < 0 || o.driver > 2) return FW_ERR_ARG;
+  if (o.grid < 0 || o.timeout_ns < 0) return FW_ERR_ARG;
+  return FW_OK;
+}
+
+fw_status solve_device(void* dist, int32_t* pred, int64_t n, int64_t ld, fw_dtype dtype,
+                       const fw_options& o, cudaStream_t s) {
+  const int BS = o.bs ? o.bs : pick_bs(n);
+  const int64_t R64 = (n + BS - 1) / BS;
+  if (R64 > 1024) return FW_ERR_UNSUPPORTED;
+  const int R = (int)R64;
+  int64_t look = o.lookahead;
+  if (look < 0) look = (int64_t)2 * num_sms();
+
+  std::lock_guard<std::mutex> lk(g_mu);
+  StreamWs* w = nullptr;
+  fw_status st = get_ws(s, solve_ws_bytes(R, BS), &w);
+  if (st != FW_OK) return st;
+  SolveWs ws = carve_solve_ws(w->base, R, BS);
+  ws.status = w->status;
+  if (w->cached_R != R || w->cached_BS != BS || w->cached_look != look) {
+    std::vector<unsigned> off(R + 2);
+    fill_stage_offsets(R, look, off.data());
+    if (cudaMemcpyAsync(ws.stage_off, off.data(), off.size() * 4, cudaMemcpyHostToDevice, s) !=
+        cudaSuccess)
+      return FW_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return FW_ERR_CUDA;
+    w->cached_R = R; w->cached_BS = BS; w->cached_look = look;
+  }
+  if (cudaMemsetAsync(ws.ver, 0, ws.flags_bytes, s) != cudaSuccess) return FW_ERR_CUDA;
+  LaunchCfg cfg;
+  cfg.BS = BS;
+  cfg.driver = o.driver == FW_DRIVER_PHASED ? 2 : 1;
+  cfg.lookahead = look;
+  cfg.grid = o.grid;
+  cfg.timeout_ns = o.timeout_ns > 0 ? o.timeout_ns : 2000000000LL;
+  cfg.packed = o.packed_keys ? 1 : 0;
+  cfg.skip_task = o.debug_skip_release;
+  cfg.ev_start = reinterpret_cast<cudaEvent_t>(o.ev_start);
+  cfg.ev_stop = reinterpret_cast<cudaEvent_t>(o.ev_stop);
+  cudaError_t e = dtype == FW_I32
+                      ? launch_solve_i32(reinterpret_cast<int32_t*>(dist), pred, n, ld, ws, cfg, s)
+                      : launch_solve_f32(reinterpret_cast<float*>(dist), pred, n, ld, ws, cfg, s);
+  return e == cudaSuccess ? FW_OK : FW_ERR_CUDA;
+}
+
+// Status word of (current device, stream); nullptr if the stream never solved.
+int* stream_status(cudaStream_t s) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(g_mu);
+  auto it = g_ws.find({dev, s});
+  return it == g_ws.end() ? nullptr : it->second.status;
+}
+
+}  // namespace fwh
+
+using namespace fwh;
+
+extern "C" {
+
+void fw_options_default(fw_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->bs = 0;
+  o->driver = FW_DRIVER_AUTO;
+  o->lookahead = -1;
+  o->grid = 0;
+  o->timeout_ns = 0;
+  o->packed_keys = 1;
+  o->debug_skip_release = -1;
+  o->ev_start = nullptr;
+  o->ev_stop = nullptr;
+}
+
+const char* fw_status_string(fw_status s) {
+  switch (s) {
+    case FW_OK: return "ok";
+    case FW_ERR_ARG: return "invalid argument";
+    case FW_ERR_CUDA: return "CUDA error";
+    case FW_ERR_TIMEOUT: return "device dependency wait timed out";
+    case FW_ERR_NEG_CYCLE: return "negative cycle (a diagonal distance is negative)";
+    case FW_ERR_NOMEM: return "out of memory";
+    case FW_ERR_UNSUPPORTED: return "unsupported dtype or size";
+  }
+  return "unknown status";
+}
+
+fw_status fw_solve_ex(void* dist, int32_t* pred, int64_t n, int64_t ld, fw_dtype dtype,
+                      const fw_options* opt, void* stream) {
+  fw_options o;
+  fw_options_default(&o);
+  if (opt) o = *opt;
+  fw_status st = check_matrix_args(dist, pred, n, ld);
+  if (st != FW_OK) return st;
+  if (dtype != FW_I32 && dtype != FW_F32) return FW_ERR_ARG;
+  if ((st = check_options(o)) != FW_OK) return st;
+  return solve_device(dist, pred, n, ld, dtype, o, reinterpret_cast<cudaStream_t>(stream));
+}
+
+fw_status fw_solve(void* dist, int32_t* pred, int64_t n, int64_t ld, fw_dtype dtype,
+                   void* stream) {
+  return fw_solve_ex(dist, pred, n, ld, dtype, nullptr, stream);
+}
+
+fw_status fw_sync_status(void* stream) {
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return FW_ERR_CUDA;
+  int* st = stream_status(s);
+  if (!st) return FW_OK;
+  int v = 0;
+  if (cudaMemcpy(&v, st, 4, cudaMemcpyDeviceToHost) != cudaSuccess) return FW_ERR_CUDA;
+  if (v) cudaMemset(st, 0, 4);
+  if (v & 1) return FW_ERR_TIMEOUT;
+  if (v & 2) return FW_ERR_NEG_CYCLE;
+  return FW_OK;
+}
+
+fw_status fw_solve_host(void* dist_host, int32_t* pred_host, int64_t n, int64_t ld,
+                        fw_dtype dtype, const fw_options* opt, void* stream) {
+  if (!dist_host || !pred_host) return FW_ERR_ARG;
+  if (n <= 0 || n > 131072 || ld < n || (ld % 4) != 0) return FW_ERR_ARG;
+  if (dtype != FW_I32 && dtype != FW_F32) return FW_ERR_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const size_t bytes = (size_t)n * ld * 4;
+  void* dd = nullptr;
+  void* dp = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return FW_ERR_CUDA;
+    StreamWs& w = g_ws[{dev, s}];
+    if (w.hbytes < bytes) {
+      if (w.hd) { cudaStreamSynchronize(s); cudaFree(w.hd); cudaFree(w.hp); w.hd = w.hp = nullptr; }
+      if (cudaMalloc(&w.hd, bytes) != cudaSuccess || cudaMalloc(&w.hp, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        if (w.hd) cudaFree(w.hd);
+        w.hd = w.hp = nullptr;
+        w.hbytes = 0;
+        return FW_ERR_NOMEM;
+      }
+      w.hbytes = bytes;
+    }
+    dd = w.hd;
+    dp = w.hp;
+  }
+  if (cudaMemcpyAsync(dd, dist_host, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return FW_ERR_CUDA;
+  fw_status st = fw_solve_ex(dd, reinterpret_cast<int32_t*>(dp), n, ld, dtype, opt, stream);
+  if (st != FW_OK) return st;
+  if (cudaMemcpyAsync(dist_host, dd, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemcpyAsync(pred_host, dp, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return FW_ERR_CUDA;
+  return fw_sync_status(stream);
+}
+
+fw_status fw_release_workspace(void) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return FW_ERR_CUDA;
+  if (cudaDeviceSynchronize() != cudaSuccess) return FW_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(g_mu);
+  for (auto it = g_ws.begin(); it != g_ws.end();) {
+    if (it->first.first == dev) {
+      StreamWs& w = it->second;
+      if (w.base) cudaFree(w.base);
+      if (w.hd) cudaFree(w.hd);
+      if (w.hp) cudaFree(w.hp);
+      if (w.sbase) cudaFree(w.sbase);
+      it = g_ws.erase(it);
+    } else {
+      ++it;
+    }
+  }
+  return FW_OK;
+}
+
+fw_status fw_queue_tasks(int32_t R, int64_t lookahead, int64_t first, int64_t count,
+                         int32_t* out) {
+  if (R < 1 || R > 1024 || lookahead < 0 || first < 0 || count < 0 || !out) return FW_ERR_ARG;
+  const int64_t total = (int64_t)R * R * R;
+  if (first + count > total) return FW_ERR_ARG;
+  std::vector<unsigned> off(R + 2);
+  fill_stage_offsets(R, lookahead, off.data());
+  if ((int64_t)off[R + 1] != total) return FW_ERR_CUDA;
+  for (int64_t t = 0; t < count; ++t) {
+    const Task k = decode_task(first + t, R, lookahead, off.data());
+    out[4 * t + 0] = k.type;
+    out[4 * t + 1] = k.r;
+    out[4 * t + 2] = k.ti;
+    out[4 * t + 3] = k.tj;
+  }
+  return FW_OK;
+}
+
+}  // extern "C"

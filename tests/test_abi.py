@@ -1,0 +1,117 @@
+"""C-ABI checks that need no GPU: the library loads, exports every entry point
+that include/fw.h declares, rejects bad arguments on the host before touching
+CUDA, and its persistent task queue is a valid topological order."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "fw.h")
+
+
+@pytest.fixture(scope="module")
+def fw():
+    import paper_2403_18619_gb300 as fw
+    from paper_2403_18619_gb300 import build
+    if not os.path.exists(fw.LIB_PATH):
+        build.build()
+    fw.load()
+    return fw
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(fw_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(fw):
+    names = declared_functions()
+    assert len(names) >= 15
+    lib = fw.load()
+    for name in names:
+        assert hasattr(lib, name), name
+    out = subprocess.run(["nm", "-D", "--defined-only", fw.LIB_PATH], capture_output=True,
+                         text=True).stdout
+    exported = set(re.findall(r" T (fw_[a-z_0-9]+)", out))
+    assert set(names) <= exported
+
+
+def test_status_strings_and_defaults(fw):
+    lib = fw.load()
+    for code in range(7):
+        assert lib.fw_status_string(code)
+    o = fw.Options.default()
+    assert o.bs == 0 and o.packed_keys == 1 and o.debug_skip_release == -1 and o.lookahead == -1
+
+
+def test_host_argument_checks(fw):
+    lib = fw.load()
+    good = 0x10000  # never dereferenced: every call below fails its host-side checks
+    I32 = fw.FW_I32
+    assert lib.fw_solve(None, good + 4096, 8, 8, I32, None) == 1
+    assert lib.fw_solve(good, good + 4096, 0, 8, I32, None) == 1
+    assert lib.fw_solve(good, good + 4096, 9, 8, I32, None) == 1       # ld < n
+    assert lib.fw_solve(good, good + 4096, 6, 6, I32, None) == 1       # ld % 4 != 0
+    assert lib.fw_solve(good + 4, good + 4096, 8, 8, I32, None) == 1   # misaligned
+    assert lib.fw_solve(good, good, 8, 8, I32, None) == 1              # aliasing
+    assert lib.fw_solve(good, good + 4096, 8, 8, 7, None) == 1         # dtype
+    bad = fw.Options.default(bs=48)
+    assert lib.fw_solve_ex(good, good + 4096, 8, 8, I32, ctypes.byref(bad), None) == 1
+    bad = fw.Options.default(driver=9)
+    assert lib.fw_solve_ex(good, good + 4096, 8, 8, I32, ctypes.byref(bad), None) == 1
+    assert lib.fw_solve_host(None, None, 8, 8, I32, None, None) == 1
+    assert lib.fw_queue_tasks(0, 0, 0, 0, None) == 1
+    assert lib.fw_verify_certificate(None, None, None, 8, 8, None, None) == 1
+
+
+def _update_task(t):
+    typ, r, i, j = t
+    return (r, i, j)
+
+
+@pytest.mark.parametrize("R", [1, 2, 3, 4, 7, 12])
+@pytest.mark.parametrize("look", [0, 5, 10 ** 6])
+def test_queue_is_complete_and_topological(fw, R, look):
+    q = fw.fw_queue_tasks(R, look)
+    assert q.shape == (R ** 3, 4)
+    pos = {}
+    for idx, (typ, r, i, j) in enumerate(q.tolist()):
+        key = (r, i, j)
+        assert key not in pos, "tile updated twice in one round"
+        pos[key] = idx
+        if i == r and j == r:
+            assert typ == 0
+        elif i == r:
+            assert typ == 1
+        elif j == r:
+            assert typ == 2
+        else:
+            assert typ == 3
+    assert len(pos) == R ** 3
+    rounds_p2 = {}
+    rounds_p3 = {}
+    for idx, (typ, r, i, j) in enumerate(q.tolist()):
+        if typ in (1, 2):
+            rounds_p2.setdefault(r, []).append(idx)
+        if typ == 3:
+            rounds_p3.setdefault(r, []).append(idx)
+    for idx, (typ, r, i, j) in enumerate(q.tolist()):
+        deps = []
+        if r >= 1:
+            deps.append(pos[(r - 1, i, j)])        # the tile's own previous round
+        if typ in (1, 2):
+            deps.append(pos[(r, r, r)])            # the closed pivot
+        if typ == 3:
+            deps.append(pos[(r, i, r)])            # column panel tile of its row
+            deps.append(pos[(r, r, j)])            # row panel tile of its column
+        if typ == 0 and r >= 2:
+            deps += rounds_p2.get(r - 2, [])       # pivot snapshot slot reuse
+        if typ in (1, 2) and r >= 2:
+            deps += rounds_p3.get(r - 2, [])       # panel snapshot slot reuse
+        for d in deps:
+            assert d < idx, (q[idx].tolist(), q[d].tolist())

@@ -1,0 +1,224 @@
+"""GPU parity of the blocked FW solve (through the C ABI) against the CPU oracle.
+
+int32: distances bit-exact, predecessors equal on every pair whose shortest
+path is unique, and the shortest-path certificate on all the rest.
+fp32: distances within 1e-6 * hops (relative) of the fp64 oracle, predecessors
+equal where the oracle's last hop wins by a margin above that tolerance.
+"""
+import numpy as np
+import pytest
+
+import graphgen
+import oracle
+from fwtest import (INF, check_f32, check_int_full, check_int_rows, fw, gpu_solve, int_case)
+
+pytestmark = pytest.mark.gpu
+
+PERSISTENT, PHASED = 1, 2
+
+
+# ------------------------------------------------------------------ int32 ---
+
+@pytest.mark.parametrize("driver", [PERSISTENT, PHASED])
+@pytest.mark.parametrize("bs", [32, 64, 128])
+@pytest.mark.parametrize("n", [1, 2, 5, 31, 33, 64, 130, 257, 600])
+def test_int_sizes(n, bs, driver):
+    W, Do, Po, cnt = int_case(n, 1000 + n, 0.35, 1, 60)
+    D, P = gpu_solve(W, bs=bs, driver=driver)
+    check_int_full(W, D, P, Do, Po, cnt)
+
+
+@pytest.mark.parametrize("driver", [PERSISTENT, PHASED])
+def test_int_config_small(driver):
+    """n=1024 complete digraph, weights uniform in [1,100], BS=32."""
+    W, Do, Po, cnt = int_case(1024, 1, 1.0, 1, 100)
+    D, P = gpu_solve(W, bs=32, driver=driver)
+    check_int_full(W, D, P, Do, Po, cnt)
+
+
+@pytest.mark.parametrize("bs", [32, 128])
+def test_int_generic_path(bs):
+    """Weights large enough that packed keys cannot hold the sums: every tile
+    takes the generic kernel; also the packed path switched off by option."""
+    n = 40
+    W = graphgen.dense_graph_i32(n, seed=77, p=0.4, lo=1 << 20, hi=(1 << 23) + 5)
+    Do, Po = oracle.fw_i64(W)
+    cnt = oracle.path_count_i64(W, Do)
+    for driver in (PERSISTENT, PHASED):
+        D, P = gpu_solve(W, bs=bs, driver=driver)
+        check_int_full(W, D, P, Do, Po, cnt)
+    W2, Do2, Po2, cnt2 = int_case(300, 5, 0.3, 1, 50)
+    D, P = gpu_solve(W2, bs=bs, packed=0)
+    check_int_full(W2, D, P, Do2, Po2, cnt2)
+
+
+def test_int_mixed_bounds():
+    """Some tiles fit the packed keys and some do not, within one solve."""
+    n = 300
+    W = graphgen.dense_graph_i32(n, seed=8, p=0.5, lo=1, hi=40)
+    big = graphgen.dense_graph_i32(n, seed=9, p=0.5, lo=1 << 19, hi=1 << 20)
+    W[:, 200:] = np.where(W[:, 200:] < INF, big[:, 200:], INF)
+    np.fill_diagonal(W, 0)
+    Do, Po = oracle.fw_i64(W)
+    cnt = oracle.path_count_i64(W, Do)
+    D, P = gpu_solve(W, bs=32)
+    check_int_full(W, D, P, Do, Po, cnt)
+
+
+def test_int_padding_untouched_and_disconnected():
+    n = 150
+    W = graphgen.dense_graph_i32(n, seed=3, p=0.2, lo=1, hi=9)
+    W[:70, 70:] = INF
+    W[70:, :70] = INF
+    np.fill_diagonal(W, 0)
+    Do, Po = oracle.fw_i64(W)
+    cnt = oracle.path_count_i64(W, Do)
+    D, P = gpu_solve(W, bs=32, extra_ld=12)
+    check_int_full(W, D, P, Do, Po, cnt)
+    assert (D[:70, 70:] == INF).all() and (P[:70, 70:] == -1).all()
+
+
+def test_int_zero_weight_edges():
+    n = 90
+    W = graphgen.dense_graph_i32(n, seed=12, p=0.3, lo=0, hi=5)
+    Do, Po = oracle.fw_i64(W)
+    D, P = gpu_solve(W, bs=32)
+    np.testing.assert_array_equal(D.astype(np.int64), Do)
+    # with zero weights pred may legitimately differ; it must still be a tight last hop
+    cert = oracle.certificate_i64(W, D, P)
+    assert cert[0] == 0 and cert[1] == 0 and cert[2] == 0
+
+
+def test_repeated_solves_share_workspace():
+    cases = [int_case(n, 50 + n, 0.5, 1, 30) for n in (200, 520, 64)]
+    for W, Do, Po, cnt in cases + cases[:1]:
+        D, P = gpu_solve(W, bs=64)
+        check_int_full(W, D, P, Do, Po, cnt)
+
+
+def test_lookahead_and_grid_variants():
+    W, Do, Po, cnt = int_case(700, 4, 0.6, 1, 80)
+    for look, grid in ((0, 0), (1, 3), (10 ** 6, 0), (-1, 1)):
+        D, P = gpu_solve(W, bs=32, lookahead=look, grid=grid)
+        check_int_full(W, D, P, Do, Po, cnt)
+
+
+def test_host_buffer_path():
+    m = fw()
+    W, Do, Po, cnt = int_case(333, 21, 0.4, 1, 99)
+    ld = m.padded(333) + 4
+    Dh = np.full((333, ld), -5, np.int32)
+    Dh[:, :333] = W
+    Ph = np.zeros((333, ld), np.int32)
+    m.fw_solve_host(Dh[:, :333], Ph[:, :333], m.Options.default(bs=64))
+    check_int_full(W, Dh[:, :333].copy(), Ph[:, :333].copy(), Do, Po, cnt)
+    assert (Dh[:, 333:] == -5).all()
+
+
+# ------------------------------------------------------------------- fp32 ---
+
+@pytest.mark.parametrize("driver", [PERSISTENT, PHASED])
+@pytest.mark.parametrize("n,bs", [(37, 32), (200, 64), (513, 128), (1000, 64)])
+def test_f32(n, bs, driver):
+    W = graphgen.dense_graph_f32(n, seed=n, p=0.5)
+    Do, Po = oracle.fw_f64(W)
+    D, P = gpu_solve(W, bs=bs, driver=driver)
+    safe = check_f32(W, D, P, Do, Po)
+    assert safe > n
+
+
+def test_f32_one_two_weights():
+    n = 400
+    W = graphgen.dense_graph_f32(n, seed=3, p=0.1, kind=graphgen.KIND_ONE_TWO)
+    Do, Po = oracle.fw_f64(W)
+    D, P = gpu_solve(W, bs=32)
+    check_f32(W, D, P, Do, Po)
+
+
+# ---------------------------------------------------------- error paths ---
+
+def test_negative_cycle_reported():
+    import torch
+    m = fw()
+    n = 64
+    W = graphgen.dense_graph_i32(n, seed=2, p=0.3, lo=1, hi=9)
+    W[5, 6], W[6, 7], W[7, 5] = 1, 1, -10
+    Wt = torch.from_numpy(W).cuda()
+    with pytest.raises(m.FWError) as e:
+        m.solve(Wt, m.Options.default(bs=32, packed_keys=0))
+    assert e.value.code == 4
+    Wf = torch.from_numpy(np.where(W >= INF, np.inf, W).astype(np.float32)).cuda()
+    with pytest.raises(m.FWError) as e:
+        m.solve(Wf, m.Options.default(bs=32))
+    assert e.value.code == 4
+    # the stream's status was cleared; a normal solve works afterwards
+    Wg, Do, Po, cnt = int_case(100, 1, 0.5, 1, 10)
+    D, P = gpu_solve(Wg, bs=32)
+    check_int_full(Wg, D, P, Do, Po, cnt)
+
+
+def test_dependency_timeout_is_reported_not_hung():
+    """A task whose completion is never published: its dependents give up after
+    the bounded wait and the host reads FW_ERR_TIMEOUT; the GPU stays usable."""
+    import torch
+    m = fw()
+    n = 256
+    W, Do, Po, cnt = int_case(n, 31, 0.5, 1, 50)
+    R = n // 32
+    q = m.fw_queue_tasks(R, 2 * 152)
+    skip = int(np.argwhere(q[:, 0] == 1)[0][0])  # first row-panel task
+    ld = m.padded(n)
+    D = torch.from_numpy(W).cuda()
+    P = torch.empty_like(D)
+    opt = m.Options.default(bs=32, debug_skip_release=skip, timeout_ns=200_000_000)
+    m.fw_solve_ex(D, P, opt)
+    with pytest.raises(m.FWError) as e:
+        m.fw_sync_status()
+    assert e.value.code == 3
+    D2, P2 = gpu_solve(W, bs=32)
+    check_int_full(W, D2, P2, Do, Po, cnt)
+
+
+# --------------------------------------------------------- verification ---
+
+def test_certificate_kernel_matches_oracle():
+    import torch
+    m = fw()
+    W, Do, Po, cnt = int_case(257, 17, 0.3, 1, 20)
+    D, P = gpu_solve(W, bs=64)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    assert m.fw_verify_certificate(t(W), t(D), t(P)).sum() == 0
+    bad = D.copy()
+    i, j = np.argwhere((Do > 0) & (Do < INF))[3]
+    bad[i, j] += 1
+    g = m.fw_verify_certificate(t(W), t(bad), t(P))
+    c = oracle.certificate_i64(W, bad, P)
+    assert g[0] == c[0] and g[1] + g[2] > 0 and c[1] + c[2] > 0
+    badp = P.copy()
+    badp[i, j] = (badp[i, j] + 1) % 257
+    assert m.fw_verify_certificate(t(W), t(D), t(badp))[1] >= 1
+
+
+def test_peak_probe_is_plausible():
+    m = fw()
+    for dt in (m.FW_I32, m.FW_F32):
+        rps, per_clk, mhz = m.fw_peak_probe(dt)
+        assert 8 <= per_clk <= 260, per_clk
+        assert 300 <= mhz <= 2200, mhz
+        assert rps > 1e12
+
+
+def test_device_generator_matches_host():
+    import torch
+    import graphgen.device as gdev
+    n = 777
+    t = torch.empty((n, 780), dtype=torch.int32, device="cuda")
+    gdev.fill_i32(t[:, :n], seed=5, p=0.3, lo=1, hi=1000)
+    np.testing.assert_array_equal(t[:, :n].cpu().numpy(),
+                                  graphgen.dense_graph_i32(n, 5, 0.3, 1, 1000))
+    f = torch.empty((n, 780), dtype=torch.float32, device="cuda")
+    gdev.fill_f32(f[:, :n], seed=6, p=0.5, kind=0)
+    np.testing.assert_array_equal(f[:, :n].cpu().numpy(), graphgen.dense_graph_f32(n, 6, 0.5))
+    gdev.fill_f32(f[:, :n], seed=6, p=0.5, kind=1)
+    np.testing.assert_array_equal(f[:, :n].cpu().numpy(),
+                                  graphgen.dense_graph_f32(n, 6, 0.5, kind=1))
