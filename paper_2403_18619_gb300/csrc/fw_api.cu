@@ -29,7 +29,8 @@ struct StreamWs {
   void* sbase = nullptr;
 };
 
-std::mutex g_mu;
+std::mutex g_mu;       // guards g_ws
+std::mutex g_sms_mu;   // guards g_sms (taken on its own, also while g_mu is held)
 std::map<std::pair<int, cudaStream_t>, StreamWs> g_ws;
 std::map<int, int> g_sms;
 
@@ -38,7 +39,7 @@ std::map<int, int> g_sms;
 int num_sms() {
   int dev = 0;
   cudaGetDevice(&dev);
-  std::lock_guard<std::mutex> lk(g_mu);
+  std::lock_guard<std::mutex> lk(g_sms_mu);
   auto it = g_sms.find(dev);
   if (it != g_sms.end()) return it->second;
   int v = 0;

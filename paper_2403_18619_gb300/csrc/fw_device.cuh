@@ -718,8 +718,9 @@ __device__ void task_minplus(const Args<T>& a, int r, int ti, int tj, void* smem
   {
     // wait for the operands (bounded: a copy that never lands is reported, not hung on)
     const uint64_t t0 = globaltimer();
+    int64_t it = 0;
     while (!mbar_try_wait(&cs->bar, phase)) {
-      if (globaltimer() - t0 > (uint64_t)a.timeout_ns) {
+      if (globaltimer() - t0 > (uint64_t)a.timeout_ns || ++it > (int64_t)1 << 26) {
         if (tid == 0) atomicOr(a.status, kStTimeout);
         break;
       }

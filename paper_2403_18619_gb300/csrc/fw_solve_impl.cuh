@@ -16,13 +16,15 @@ __device__ __forceinline__ bool wait_ge(const int* p, int target, int* abort_fla
                                         int64_t timeout_ns) {
   if (ld_acquire(p) >= target) return true;
   const uint64_t t0 = globaltimer();
+  // iteration cap as well as the clock: each iteration sleeps >= 32 ns
+  const int64_t max_it = timeout_ns / 32 + 1024;
   unsigned ns = 32;
-  for (;;) {
+  for (int64_t it = 0;; ++it) {
     __nanosleep(ns);
     if (ns < 256) ns <<= 1;
     if (ld_acquire(p) >= target) return true;
     if (ld_relaxed(abort_flag)) return false;
-    if (globaltimer() - t0 > (uint64_t)timeout_ns) {
+    if (globaltimer() - t0 > (uint64_t)timeout_ns || it > max_it) {
       atomicOr(status, kStTimeout);
       atomicExch(abort_flag, 1);
       return false;
