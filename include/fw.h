@@ -205,6 +205,35 @@ fw_status fw_verify_certificate(const int32_t* W, const int32_t* dist, const int
                                 int64_t n, int64_t ld, int64_t* bad, void* stream);
 
 /*
+ * fw_solve_noalloc: fw_solve for callers that cannot allocate device memory.
+ * There is no counterpart in the paper; it exists for integrators.
+ *
+ * fw_solve obtains its workspace with cudaMalloc.  Callers that run under a
+ * device-memory budget owned by another allocator (a framework's caching pool,
+ * a server that reserved all free memory up front), or that cannot afford the
+ * device-wide synchronisation cudaMalloc may imply, use this entry point: it
+ * calls no cudaMalloc, cudaFree or other allocating routine.  Its workspace is
+ * one static device array of 12 MiB inside the library, which every GPU that
+ * loads the library's kernels holds until the process exits.
+ *
+ *   dist, pred, ld, dtype  as for fw_solve (device pointers, caller-owned).
+ *   n                      1 <= n <= 4096; larger n returns FW_ERR_UNSUPPORTED
+ *                          (use fw_solve).  BS is 32 for n <= 512, else 64.
+ *   stream                 the solve is enqueued on it and waited for.
+ * Synchronous: returns after the solve has finished, with FW_OK or the
+ * device-side error (FW_ERR_TIMEOUT, FW_ERR_NEG_CYCLE) of this call.
+ *
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress with that device current) and caches it; make that
+ * first call before any stream capture on the device.  Every call, from any
+ * thread or stream, uses the same array and clears the parts that must start
+ * at zero; calls whose executions overlap on the GPU race on it and produce
+ * wrong results, so serialise them (one at a time per device).
+ */
+fw_status fw_solve_noalloc(void* dist, int32_t* pred, int64_t n, int64_t ld, fw_dtype dtype,
+                           void* stream);
+
+/*
  * fw_queue_tasks: diagnostic view of the persistent driver's task queue for R
  * tile rows (R = ceil(n / BS)) and a given lookahead (the value fw_options
  * .lookahead resolves to).  Writes 4 int32 per task -- type (0 pivot, 1 row

@@ -95,11 +95,12 @@ def load():
         lib.fw_peak_probe.argtypes = [I32, P, P, P, P]
         lib.fw_verify_certificate.argtypes = [P, P, P, I64, I64, P, P]
         lib.fw_queue_tasks.argtypes = [I32, I64, I64, I64, P]
+        lib.fw_solve_noalloc.argtypes = [P, P, I64, I64, I32, P]
         for name in ("fw_solve", "fw_solve_ex", "fw_solve_host", "fw_batched_plan_create",
                      "fw_solve_batched", "fw_batched_plan_info", "fw_batched_plan_destroy",
                      "fw_backward", "fw_backward_strided", "fw_sync_status",
                      "fw_release_workspace", "fw_peak_probe", "fw_verify_certificate",
-                     "fw_queue_tasks"):
+                     "fw_queue_tasks", "fw_solve_noalloc"):
             getattr(lib, name).restype = I32
         _lib = lib
         return lib
@@ -157,6 +158,17 @@ def fw_solve_ex(dist, pred, options: Options | None = None, stream=None) -> None
     o = ctypes.byref(options) if options is not None else None
     check(load().fw_solve_ex(dp, pp, n, ld, _dtype_code(dist), o, _stream_ptr(stream)),
           "fw_solve_ex")
+
+
+def fw_solve_noalloc(dist, pred, stream=None) -> None:
+    """fw_solve_noalloc on CUDA tensors: the solve without any device allocation
+    (workspace in a fixed static device array; n <= 4096; synchronous)."""
+    dp, n, ld = _matrix(dist, "dist")
+    pp, n2, ld2 = _matrix(pred, "pred")
+    if n2 != n or ld2 != ld:
+        raise ValueError("dist and pred must have the same shape and row stride")
+    check(load().fw_solve_noalloc(dp, pp, n, ld, _dtype_code(dist), _stream_ptr(stream)),
+          "fw_solve_noalloc")
 
 
 def fw_solve_host(dist: np.ndarray, pred: np.ndarray, options: Options | None = None,
