@@ -89,6 +89,12 @@ typedef struct fw_options {
                                  this task index, so that its dependents time out; -1 = off */
   void* ev_start;             /* optional cudaEvent_t recorded just before the solver kernels */
   void* ev_stop;              /* optional cudaEvent_t recorded just after them */
+  uint64_t* trace;            /* optional device buffer of trace_cap x 10 uint64: a %globaltimer
+                                 timeline of every trace_stride-th task of the persistent driver
+                                 (claim, inputs ready, operands issued, published; compute start
+                                 and end), the GPU view of the idle time Opt-9 targets (Sec. 4.3) */
+  int64_t trace_cap;
+  int32_t trace_stride;
 } fw_options;
 
 /* Fills *opt with the defaults used by fw_solve. */

@@ -49,6 +49,9 @@ class Options(ctypes.Structure):
         ("debug_skip_release", ctypes.c_int32),
         ("ev_start", ctypes.c_void_p),
         ("ev_stop", ctypes.c_void_p),
+        ("trace", ctypes.c_void_p),
+        ("trace_cap", ctypes.c_int64),
+        ("trace_stride", ctypes.c_int32),
     ]
 
     @classmethod

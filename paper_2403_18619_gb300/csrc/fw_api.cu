@@ -130,6 +130,7 @@ fw_status check_options(const fw_options& o) {
   if (o.bs != 0 && o.bs != 32 && o.bs != 64 && o.bs != 128) return FW_ERR_ARG;
   if (o.driver < 0 || o.driver > 2) return FW_ERR_ARG;
   if (o.grid < 0 || o.timeout_ns < 0) return FW_ERR_ARG;
+  if (o.trace && (o.trace_cap <= 0 || o.trace_cap > (1 << 30) || o.trace_stride <= 0)) return FW_ERR_ARG;
   return FW_OK;
 }
 
@@ -168,6 +169,9 @@ fw_status solve_device(void* dist, int32_t* pred, int64_t n, int64_t ld, fw_dtyp
   cfg.skip_task = o.debug_skip_release;
   cfg.ev_start = reinterpret_cast<cudaEvent_t>(o.ev_start);
   cfg.ev_stop = reinterpret_cast<cudaEvent_t>(o.ev_stop);
+  cfg.trace = o.trace;
+  cfg.trace_cap = o.trace_cap;
+  cfg.trace_stride = o.trace_stride;
   cudaError_t e = dtype == FW_I32
                       ? launch_solve_i32(reinterpret_cast<int32_t*>(dist), pred, n, ld, ws, cfg, s)
                       : launch_solve_f32(reinterpret_cast<float*>(dist), pred, n, ld, ws, cfg, s);
@@ -201,6 +205,9 @@ void fw_options_default(fw_options* o) {
   o->debug_skip_release = -1;
   o->ev_start = nullptr;
   o->ev_stop = nullptr;
+  o->trace = nullptr;
+  o->trace_cap = 0;
+  o->trace_stride = 0;
 }
 
 const char* fw_status_string(fw_status s) {

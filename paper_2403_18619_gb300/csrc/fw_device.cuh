@@ -110,6 +110,15 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned phase) {
   return ok != 0;
 }
 
+// Barrier over the 256 compute threads (warps 0-7).  In kernels that add a
+// producer warp, that warp does not take part; in 256-thread kernels this is
+// the whole CTA.
+__device__ __forceinline__ void bar_compute() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 // ------------------------------------------------------------- geometry ----
 
 // Thread micro-tile layout for a BS x BS tile and 256 threads (16 x 16):
@@ -218,6 +227,10 @@ struct Args {
   T* rowR;              // raw
   int32_t* rowP;        // [2][tiles][BS*BS] predecessors of the row panel tiles
   int32_t* rowB;
+  // optional per-task trace (persistent driver)
+  uint64_t* trace;
+  int trace_cap;
+  int trace_stride;
 };
 
 // -------------------------------------------------------- shared memory ----
@@ -352,9 +365,9 @@ __device__ __forceinline__ void block_max2(int& a, int& b, CtaScratch* cs) {
     b = max(b, __shfl_xor_sync(0xffffffffu, b, o));
   }
   const int w = threadIdx.x >> 5;
-  __syncthreads();
+  bar_compute();
   if ((threadIdx.x & 31) == 0) { cs->red[0][w] = a; cs->red[1][w] = b; }
-  __syncthreads();
+  bar_compute();
   a = cs->red[0][0];
   b = cs->red[1][0];
 #pragma unroll
@@ -365,7 +378,7 @@ __device__ __forceinline__ void block_max2(int& a, int& b, CtaScratch* cs) {
 
 // acc[m][n] = min(acc[m][n], min_kk key(A[kk][row m]) + key(B[kk][col n]))
 // over packed keys: one __viaddmin_u32 (DPX) per relaxation.
-template <int BS>
+template <int BS, int K = BS>
 __device__ __forceinline__ void core_packed(const uint32_t* __restrict__ As,
                                             const uint32_t* __restrict__ Bs,
                                             uint32_t (&acc)[Geo<BS>::TM][Geo<BS>::TM], int tx,
@@ -373,7 +386,7 @@ __device__ __forceinline__ void core_packed(const uint32_t* __restrict__ As,
   using Gm = Geo<BS>;
   constexpr int G = Gm::G, TM = Gm::TM;
 #pragma unroll 2
-  for (int kk = 0; kk < BS; ++kk) {
+  for (int kk = 0; kk < K; ++kk) {
     uint32_t a[TM], b[TM];
 #pragma unroll
     for (int g = 0; g < Gm::NG; ++g) {
@@ -393,14 +406,15 @@ __device__ __forceinline__ void core_packed(const uint32_t* __restrict__ As,
 // Generic relaxation with an explicit first-argmin: s = A + B; if (s < acc)
 // { acc = s; arg = kk + 1 }.  Used for fp32 and for int32 tiles whose values
 // exceed the packed-key bound.
-template <int BS, typename T>
+template <int BS, typename T, int K = BS>
 __device__ __forceinline__ void core_generic(const T* __restrict__ As, const T* __restrict__ Bs,
                                              T (&acc)[Geo<BS>::TM][Geo<BS>::TM],
-                                             int (&arg)[Geo<BS>::TM][Geo<BS>::TM], int tx, int ty) {
+                                             int (&arg)[Geo<BS>::TM][Geo<BS>::TM], int tx, int ty,
+                                             int kk0 = 0) {
   using Gm = Geo<BS>;
   constexpr int G = Gm::G, TM = Gm::TM;
 #pragma unroll 1
-  for (int kk = 0; kk < BS; ++kk) {
+  for (int kk = 0; kk < K; ++kk) {
     T a[TM], b[TM];
 #pragma unroll
     for (int g = 0; g < Gm::NG; ++g) {
@@ -417,7 +431,7 @@ __device__ __forceinline__ void core_generic(const T* __restrict__ As, const T* 
         T s = a[m] + b[nn];
         bool lt = s < acc[m][nn];
         acc[m][nn] = lt ? s : acc[m][nn];
-        arg[m][nn] = lt ? kk + 1 : arg[m][nn];
+        arg[m][nn] = lt ? kk0 + kk + 1 : arg[m][nn];
       }
   }
 }
@@ -463,7 +477,7 @@ __device__ __noinline__ void task_pivot(const Args<T>& a, int r, void* smem_raw,
 #pragma unroll
           for (int mm = 0; mm < TM; ++mm) colD[buf * BS + Gm::idx(ty, mm)] = d[mm][m];
         }
-        __syncthreads();
+        bar_compute();
         T cv[TM], rv[TM];
         int32_t rp[TM];
 #pragma unroll
@@ -577,7 +591,7 @@ __device__ __noinline__ void task_panel(const Args<T>& a, int r, int t, bool is_
       put_tile<BS, false>(Bst, pv, tx, ty);
     }
   }
-  __syncthreads();
+  bar_compute();
 
   // relax; afterwards s[][] holds the new values and code[][] the argmin + 1 (0 = unchanged)
   int code[TM][TM];
@@ -629,7 +643,7 @@ __device__ __noinline__ void task_panel(const Args<T>& a, int r, int t, bool is_
       }
     }
   }
-  __syncthreads();
+  bar_compute();
   store_tile<BS>(a.D, s, a.n, a.ld, ti, tj, tx, ty);
   store_tile<BS>(a.P, np, a.n, a.ld, ti, tj, tx, ty);
 

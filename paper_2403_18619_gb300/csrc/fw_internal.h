@@ -132,6 +132,9 @@ struct LaunchCfg {
   int packed;
   int skip_task;
   cudaEvent_t ev_start, ev_stop;
+  uint64_t* trace = nullptr;
+  int64_t trace_cap = 0;
+  int trace_stride = 0;
 };
 
 // Enqueue one solve (init + driver).  Returns a cudaError_t.

@@ -79,13 +79,13 @@ cudaError_t run(T* D, int32_t* P, int64_t n, int64_t ld, unsigned char* base, in
   k_init_pred<T><<<(int)blocks, 256, 0, s>>>(D, P, n, ld);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
 
-  const size_t smem = Smem<BS>::bytes();
-  auto kern = k_persistent<T, BS>;
+  const size_t smem = WsLayout<BS>::bytes();
+  auto kern = k_persistent_ws<T, BS>;
   if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
       cudaSuccess)
     return e;
   int occ = 0;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, smem)) !=
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kWsThreads, smem)) !=
       cudaSuccess)
     return e;
   int64_t grid = (int64_t)(occ > 0 ? occ : 1) * sms;
@@ -93,7 +93,7 @@ cudaError_t run(T* D, int32_t* P, int64_t n, int64_t ld, unsigned char* base, in
   if (grid > total) grid = total;
   cudaLaunchConfig_t lc{};
   lc.gridDim = dim3((unsigned)grid);
-  lc.blockDim = dim3(kThreads);
+  lc.blockDim = dim3(kWsThreads);
   lc.dynamicSmemBytes = smem;
   lc.stream = s;
   cudaLaunchAttribute attr[1];

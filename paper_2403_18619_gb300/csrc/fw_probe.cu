@@ -4,7 +4,7 @@
 // relaxes it with the same instruction the solver issues per relaxation:
 //   int32: acc = __viaddmin_u32(a, b, acc)     (one DPX instruction)
 //   fp32 : acc = fminf(a + b, acc)             (add + min)
-// The row operands a[m] are refreshed every step from the chains themselves,
+// The row operands a[m] are refreshed every 4 steps from the chains themselves,
 // so the loop carries a real dependence and nothing can be hoisted out of it.
 // One CTA of 512 threads per SM; %clock64 around the loop gives the SM-clock
 // rate, CUDA events the wall-clock rate.
@@ -33,18 +33,20 @@ __global__ void __launch_bounds__(kProbeThreads, 1)
   __syncthreads();
   const long long c0 = clock64();
 #pragma unroll 1
-  for (int it = 0; it < iters; ++it) {
+  for (int it = 0; it < iters; it += 4) {
 #pragma unroll
-    for (int m = 0; m < 8; ++m)
+    for (int u = 0; u < 4; ++u)
 #pragma unroll
-      for (int n = 0; n < 8; ++n) {
-        if constexpr (kInt) {
-          acc[m][n] = __viaddmin_u32(a[m], b[n], acc[m][n]);
-        } else {
-          float x = __uint_as_float(a[m]) + __uint_as_float(b[n]);
-          acc[m][n] = __float_as_uint(fminf(x, __uint_as_float(acc[m][n])));
+      for (int m = 0; m < 8; ++m)
+#pragma unroll
+        for (int n = 0; n < 8; ++n) {
+          if constexpr (kInt) {
+            acc[m][n] = __viaddmin_u32(a[m], b[n], acc[m][n]);
+          } else {
+            float x = __uint_as_float(a[m]) + __uint_as_float(b[n]);
+            acc[m][n] = __float_as_uint(fminf(x, __uint_as_float(acc[m][n])));
+          }
         }
-      }
 #pragma unroll
     for (int m = 0; m < 8; ++m) a[m] = acc[m][m];
   }

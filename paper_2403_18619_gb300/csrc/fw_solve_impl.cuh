@@ -4,104 +4,9 @@
 
 #include "fw_device.cuh"
 #include "fw_internal.h"
+#include "fw_ws.cuh"
 
 namespace fwk {
-
-// ----------------------------------------------------- persistent driver ----
-
-// Bounded wait until *p >= target (thread 0 only).  Gives up when another CTA
-// has aborted or when the wait exceeds timeout_ns; then records the timeout
-// and raises the abort flag so that every other CTA stops too.
-__device__ __forceinline__ bool wait_ge(const int* p, int target, int* abort_flag, int* status,
-                                        int64_t timeout_ns) {
-  if (ld_acquire(p) >= target) return true;
-  const uint64_t t0 = globaltimer();
-  // iteration cap as well as the clock: each iteration sleeps >= 32 ns
-  const int64_t max_it = timeout_ns / 32 + 1024;
-  unsigned ns = 32;
-  for (int64_t it = 0;; ++it) {
-    __nanosleep(ns);
-    if (ns < 256) ns <<= 1;
-    if (ld_acquire(p) >= target) return true;
-    if (ld_relaxed(abort_flag)) return false;
-    if (globaltimer() - t0 > (uint64_t)timeout_ns || it > max_it) {
-      atomicOr(status, kStTimeout);
-      atomicExch(abort_flag, 1);
-      return false;
-    }
-  }
-}
-
-template <typename T>
-__device__ bool wait_deps(const Args<T>& a, const fwh::Task& k) {
-  const int R = a.R;
-  const int* ver = a.ver;
-  auto w = [&](const int* p, int target) {
-    return wait_ge(p, target, a.abort_flag, a.status, a.timeout_ns);
-  };
-  const int* done2 = reinterpret_cast<const int*>(a.ctr + 1);
-  const int* done3 = reinterpret_cast<const int*>(a.ctr + 2);
-  switch (k.type) {
-    case 0:  // pivot: its tile after round r-1; pivot slot free (panels of r-2 done)
-      if (!w(ver + (size_t)k.r * R + k.r, k.r)) return false;
-      if (k.r >= 2 && !w(done2, 2 * (R - 1) * (k.r - 1))) return false;
-      return true;
-    case 1:
-    case 2:  // panel: its tile after round r-1, the pivot of r, snapshot slot free
-      if (!w(ver + (size_t)k.ti * R + k.tj, k.r)) return false;
-      if (!w(ver + (size_t)k.r * R + k.r, k.r + 1)) return false;
-      if (k.r >= 2 && !w(done3, (R - 1) * (R - 1) * (k.r - 1))) return false;
-      return true;
-    default:  // remaining tile: itself after r-1, both panels of round r
-      if (!w(ver + (size_t)k.ti * R + k.tj, k.r)) return false;
-      if (!w(ver + (size_t)k.ti * R + k.r, k.r + 1)) return false;
-      if (!w(ver + (size_t)k.r * R + k.tj, k.r + 1)) return false;
-      return true;
-  }
-}
-
-template <typename T>
-__device__ __forceinline__ void publish(const Args<T>& a, const fwh::Task& k) {
-  st_release(a.ver + (size_t)k.ti * a.R + k.tj, k.r + 1);
-  if (k.type == 1 || k.type == 2) red_release_add(a.ctr + 1, 1u);
-  if (k.type == 3) red_release_add(a.ctr + 2, 1u);
-}
-
-template <typename T, int BS>
-__global__ void __launch_bounds__(kThreads, 1) k_persistent(Args<T> a) {
-  extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ CtaScratch cs;
-  const int tid = threadIdx.x;
-  if (tid == 0) {
-    mbar_init(&cs.bar, 1);
-    fence_mbar_init();
-  }
-  __syncthreads();
-  unsigned phase = 0;
-  const int64_t total = a.stage_off[a.R + 1];
-  for (;;) {
-    if (tid == 0) {
-      const int64_t t = atomicAdd(a.ctr, 1u);
-      int ok = t < total && !ld_relaxed(a.abort_flag);
-      if (ok) ok = wait_deps(a, fwh::decode_task(t, a.R, a.lookahead, a.stage_off));
-      if (ok) fence_proxy_async();
-      cs.task = ok ? (int)t : -1;
-    }
-    __syncthreads();
-    const int t = cs.task;
-    if (t < 0) break;
-    const fwh::Task k = fwh::decode_task(t, a.R, a.lookahead, a.stage_off);
-    if (k.type == 0) {
-      task_pivot<T, BS>(a, k.r, smem, &cs);
-    } else if (k.type == 3) {
-      task_minplus<T, BS>(a, k.r, k.ti, k.tj, smem, &cs, phase);
-    } else {
-      task_panel<T, BS>(a, k.r, k.type == 1 ? k.tj : k.ti, k.type == 1, smem, &cs);
-    }
-    __syncthreads();
-    if (tid == 0 && t != a.skip_task) publish(a, k);
-  }
-}
 
 // -------------------------------------------------------- phased driver ----
 
@@ -150,6 +55,7 @@ cudaError_t launch_bs(T* D, int32_t* P, int64_t n, int64_t ld, const fwh::SolveW
   a.piv = reinterpret_cast<T*>(ws.piv); a.pivP = ws.pivP;
   a.colK = ws.colK; a.colR = reinterpret_cast<T*>(ws.colR); a.colB = ws.colB;
   a.rowK = ws.rowK; a.rowR = reinterpret_cast<T*>(ws.rowR); a.rowP = ws.rowP; a.rowB = ws.rowB;
+  a.trace = cfg.trace; a.trace_cap = (int)cfg.trace_cap; a.trace_stride = cfg.trace_stride;
   const int R = ws.R;
   const size_t smem = Smem<BS>::bytes();
   cudaError_t e;
@@ -179,12 +85,13 @@ cudaError_t launch_bs(T* D, int32_t* P, int64_t n, int64_t ld, const fwh::SolveW
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
   } else {
-    auto kern = k_persistent<T, BS>;
+    auto kern = k_persistent_ws<T, BS>;
+    const size_t wsmem = WsLayout<BS>::bytes();
     static int occ = -1;
     if (occ < 0) {
-      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsmem);
       int o = 0;
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, kThreads, smem);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, kWsThreads, wsmem);
       occ = o > 0 ? o : 1;
     }
     int64_t grid = cfg.grid > 0 ? cfg.grid : (int64_t)occ * fwh::num_sms();
@@ -194,8 +101,8 @@ cudaError_t launch_bs(T* D, int32_t* P, int64_t n, int64_t ld, const fwh::SolveW
     if (grid < 1) grid = 1;
     cudaLaunchConfig_t lc{};
     lc.gridDim = dim3((unsigned)grid);
-    lc.blockDim = dim3(kThreads);
-    lc.dynamicSmemBytes = smem;
+    lc.blockDim = dim3(kWsThreads);
+    lc.dynamicSmemBytes = wsmem;
     lc.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;

@@ -1,0 +1,490 @@
+// Warp-specialised persistent driver (the GPU form of Opt-9's intra-round
+// concurrency, Sec. 3.2, extended across rounds as the paper's future work
+// proposes, Sec. 5).
+//
+// A CTA has 8 compute warps, 1 producer warp and 1 publisher warp.  The
+// publisher sleeps on the compute warps' task-done barrier and publishes each
+// finished tile (the GPU-scope release), so that neither the compute warps nor
+// the producer wait on that fence.  The producer claims tasks
+// from the global queue in order, waits (bounded) on the tiles' ready flags,
+// and streams the operands of the remaining-tile tasks into shared memory with
+// TMA bulk copies while the compute warps work on the previous task:
+//   * the tile's own D block (one bulk copy per row)          -> Dbuf
+//   * the A and B panel snapshots, 32 k-steps per chunk       -> 2-stage ring
+//   * the predecessor tile of the B panel (for the epilogue)  -> Pbuf
+// mbarriers carry "full" (transaction bytes landed) and "empty" (compute
+// warps done reading) signals.  Pivot and panel tasks are run by the compute
+// warps alone (they use the ring and Dbuf as scratch); the producer waits for
+// them to finish before it touches shared memory again.
+#pragma once
+
+#include "fw_device.cuh"
+#include "fw_internal.h"
+
+namespace fwk {
+
+// 10 warps: 8 compute, 1 producer, 1 publisher.  Three of them share one SM
+// sub-partition, whose 16K registers then cap the kernel at 168 registers per
+// thread (ptxas derives this from the launch bounds).
+constexpr int kWsThreads = kThreads + 64;
+constexpr int kPubDepth = 4;  // tasks handed to the compute warps but not yet published
+constexpr int kCK = 32;  // k-steps per streamed chunk
+
+template <int BS>
+struct WsLayout {
+  static constexpr int NC = BS / kCK;                      // chunks per task
+  static constexpr size_t kChunkBytes = (size_t)kCK * BS * 4;  // one operand chunk
+  static constexpr size_t kStage = 2 * kChunkBytes;        // A chunk + B chunk
+  static constexpr size_t kRing = 2 * kStage;
+  static constexpr size_t kTile = (size_t)BS * BS * 4;
+  __host__ __device__ static constexpr size_t ring_off() { return 0; }
+  __host__ __device__ static constexpr size_t d_off() { return kRing; }
+  __host__ __device__ static constexpr size_t p_off() { return kRing + kTile; }
+  __host__ __device__ static constexpr size_t bytes() { return kRing + 2 * kTile; }
+  static_assert(kRing >= kTile, "pivot/panel tasks use the ring as a full tile buffer");
+};
+
+struct WsBars {
+  uint64_t desc_full[2], desc_empty[2];
+  uint64_t chunk_full[2], chunk_empty[2];
+  uint64_t d_full, d_empty, p_full, p_empty, task_done;
+  uint64_t pub_full[kPubDepth], pub_empty[kPubDepth];
+  int desc[2][8];           // t, type, r, ti, tj, fast
+  int pubq[kPubDepth][5];   // t, type, r, ti, tj of tasks awaiting publication
+};
+
+// Bounded wait on an mbarrier phase; false (and the timeout status) on expiry.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, int* status,
+                                          int* abort_flag, int64_t timeout_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = globaltimer();
+  for (int64_t it = 0; it < ((int64_t)1 << 26); ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 255) == 255 && globaltimer() - t0 > (uint64_t)timeout_ns) break;
+  }
+  atomicOr(status, kStTimeout);
+  atomicExch(abort_flag, 1);
+  return false;
+}
+
+// Scalars the compute warps need, passed by value (kept in registers).
+template <typename T>
+struct TileCtx {
+  T* D;
+  int32_t* P;
+  int64_t n, ld;
+  int* status;
+  int* abort_flag;
+  int64_t timeout_ns;
+};
+
+// Compute-warp side of a remaining-tile task (phase 4 of round r, tile ti,tj).
+// Returns false if an operand never arrived (the kernel then stops).
+template <typename T, int BS>
+__device__ __noinline__ bool ws_minplus(TileCtx<T> c, int ti, int tj, bool fast,
+                                        unsigned char* smem, WsBars* wb, unsigned& dcnt,
+                                        unsigned& ccnt, unsigned& pcnt) {
+  using Gm = Geo<BS>;
+  using K = Keys<BS>;
+  using L = WsLayout<BS>;
+  constexpr int TM = Gm::TM, G = Gm::G;
+  constexpr bool kInt = Num<T>::kInt;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4, lane = tid & 31;
+  const T* Dbuf = reinterpret_cast<const T*>(smem + L::d_off());
+  const int32_t* Pbuf = reinterpret_cast<const int32_t*>(smem + L::p_off());
+  unsigned char* ring = smem + L::ring_off();
+  const int64_t row0 = (int64_t)ti * BS, col0 = (int64_t)tj * BS;
+  const int nrow = (int)(c.n - row0 < BS ? c.n - row0 : BS);  // valid rows / columns of the tile
+  const int ncol = (int)(c.n - col0 < BS ? c.n - col0 : BS);
+
+  // 1. the tile's current values (rows/columns beyond n read as INF)
+  if (!mbar_wait(&wb->d_full, dcnt & 1, c.status, c.abort_flag, c.timeout_ns)) return false;
+  T old[TM][TM];
+#pragma unroll
+  for (int m = 0; m < TM; ++m) {
+    const int lr = Gm::idx(ty, m);
+#pragma unroll
+    for (int g = 0; g < Gm::NG; ++g) {
+      const int lc0 = g * Gm::SPAN + tx * G;
+      T tmp[G];
+      vload_s<G>(tmp, Dbuf + lr * BS + lc0);
+#pragma unroll
+      for (int e = 0; e < G; ++e)
+        old[m][g * G + e] = (lr < nrow && lc0 + e < ncol) ? tmp[e] : Num<T>::inf();
+    }
+  }
+  __syncwarp();
+  if (lane == 0) mbar_arrive(&wb->d_empty);
+  ++dcnt;
+
+  T* Drow = c.D + row0 * c.ld + col0;
+  int32_t* Prow = c.P + row0 * c.ld + col0;
+  bool neg = false;
+  if (fast) {
+    uint32_t acc[TM][TM];
+#pragma unroll
+    for (int m = 0; m < TM; ++m)
+#pragma unroll
+      for (int nn = 0; nn < TM; ++nn) acc[m][nn] = kInt ? key_of<BS>((int32_t)old[m][nn]) : 0u;
+    for (int ch = 0; ch < L::NC; ++ch) {
+      const unsigned st = ccnt & 1;
+      if (!mbar_wait(&wb->chunk_full[st], (ccnt >> 1) & 1, c.status, c.abort_flag, c.timeout_ns))
+        return false;
+      const uint32_t* As = reinterpret_cast<const uint32_t*>(ring + st * L::kStage);
+      const uint32_t* Bs = As + kCK * BS;
+      core_packed<BS, kCK>(As, Bs, acc, tx, ty);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&wb->chunk_empty[st]);
+      ++ccnt;
+    }
+    if (!mbar_wait(&wb->p_full, pcnt & 1, c.status, c.abort_flag, c.timeout_ns)) return false;
+#pragma unroll
+    for (int m = 0; m < TM; ++m) {
+      const int lr = Gm::idx(ty, m);
+#pragma unroll
+      for (int nn = 0; nn < TM; ++nn) {
+        const uint32_t code = acc[m][nn] & K::MASK;
+        const int lc = Gm::idx(tx, nn);
+        if (code && lr < nrow && lc < ncol) {
+          const int32_t nv = (int32_t)(acc[m][nn] >> K::KB);
+          Drow[lr * c.ld + lc] = (T)nv;
+          Prow[lr * c.ld + lc] = Pbuf[(code - 1) * BS + lc];
+          neg |= (row0 + lr == col0 + lc) && nv < 0;
+        }
+      }
+    }
+  } else {
+    int arg[TM][TM];
+#pragma unroll
+    for (int m = 0; m < TM; ++m)
+#pragma unroll
+      for (int nn = 0; nn < TM; ++nn) arg[m][nn] = 0;
+    for (int ch = 0; ch < L::NC; ++ch) {
+      const unsigned st = ccnt & 1;
+      if (!mbar_wait(&wb->chunk_full[st], (ccnt >> 1) & 1, c.status, c.abort_flag, c.timeout_ns))
+        return false;
+      const T* As = reinterpret_cast<const T*>(ring + st * L::kStage);
+      const T* Bs = As + kCK * BS;
+      core_generic<BS, T, kCK>(As, Bs, old, arg, tx, ty, ch * kCK);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&wb->chunk_empty[st]);
+      ++ccnt;
+    }
+    if (!mbar_wait(&wb->p_full, pcnt & 1, c.status, c.abort_flag, c.timeout_ns)) return false;
+#pragma unroll
+    for (int m = 0; m < TM; ++m) {
+      const int lr = Gm::idx(ty, m);
+#pragma unroll
+      for (int nn = 0; nn < TM; ++nn) {
+        const int lc = Gm::idx(tx, nn);
+        if (arg[m][nn] && lr < nrow && lc < ncol) {
+          Drow[lr * c.ld + lc] = old[m][nn];
+          Prow[lr * c.ld + lc] = Pbuf[(arg[m][nn] - 1) * BS + lc];
+          neg |= (row0 + lr == col0 + lc) && old[m][nn] < T(0);
+        }
+      }
+    }
+  }
+  __syncwarp();
+  if (lane == 0) mbar_arrive(&wb->p_empty);
+  ++pcnt;
+  if (neg) atomicOr(c.status, kStNegCycle);
+  return true;
+}
+
+// ----------------------------------------------------- persistent driver ----
+
+// Bounded wait until *p >= target (producer lane only).  `idle()` runs on
+// every poll (the producer publishes its previous task from there, so that a
+// task never waits on a task whose publication it is itself holding up).
+// Gives up when another CTA has aborted or when the wait exceeds timeout_ns;
+// then records the timeout and raises the abort flag so that every CTA stops.
+template <typename Idle>
+__device__ __forceinline__ bool wait_ge(const int* p, int target, int* abort_flag, int* status,
+                                        int64_t timeout_ns, Idle&& idle) {
+  if (ld_acquire(p) >= target) return true;
+  const uint64_t t0 = globaltimer();
+  // iteration cap as well as the clock: each iteration sleeps >= 32 ns
+  const int64_t max_it = timeout_ns / 32 + 1024;
+  unsigned ns = 32;
+  for (int64_t it = 0;; ++it) {
+    idle();
+    __nanosleep(ns);
+    if (ns < 256) ns <<= 1;
+    if (ld_acquire(p) >= target) return true;
+    if (ld_relaxed(abort_flag)) return false;
+    if (globaltimer() - t0 > (uint64_t)timeout_ns || it > max_it) {
+      atomicOr(status, kStTimeout);
+      atomicExch(abort_flag, 1);
+      return false;
+    }
+  }
+}
+
+// Inputs of task k (Sec. 2.3.1 phase order, Opt-9's per-block dependencies of
+// Sec. 3.2, and the slot reuse of the double-buffered snapshots).
+template <typename T, typename Idle>
+__device__ bool wait_deps(const Args<T>& a, const fwh::Task& k, Idle&& idle) {
+  const int R = a.R;
+  const int* ver = a.ver;
+  auto w = [&](const int* p, int target) {
+    return wait_ge(p, target, a.abort_flag, a.status, a.timeout_ns, idle);
+  };
+  const int* done2 = reinterpret_cast<const int*>(a.ctr + 1);
+  const int* done3 = reinterpret_cast<const int*>(a.ctr + 2);
+  switch (k.type) {
+    case 0:  // pivot: its tile after round r-1; pivot slot free (panels of r-2 done)
+      if (!w(ver + (size_t)k.r * R + k.r, k.r)) return false;
+      if (k.r >= 2 && !w(done2, 2 * (R - 1) * (k.r - 1))) return false;
+      return true;
+    case 1:
+    case 2:  // panel: its tile after round r-1, the pivot of r, snapshot slot free
+      if (!w(ver + (size_t)k.ti * R + k.tj, k.r)) return false;
+      if (!w(ver + (size_t)k.r * R + k.r, k.r + 1)) return false;
+      if (k.r >= 2 && !w(done3, (R - 1) * (R - 1) * (k.r - 1))) return false;
+      return true;
+    default:  // remaining tile: itself after r-1, both panels of round r
+      if (!w(ver + (size_t)k.ti * R + k.tj, k.r)) return false;
+      if (!w(ver + (size_t)k.ti * R + k.r, k.r + 1)) return false;
+      if (!w(ver + (size_t)k.r * R + k.tj, k.r + 1)) return false;
+      return true;
+  }
+}
+
+// Completion of task k: the tile's version, and the per-phase counters that
+// guard snapshot slot reuse.  Release semantics make every store of the task
+// (made by the compute warps and ordered before this thread through the
+// task_done mbarrier) visible to whoever acquires the flag.
+template <typename T>
+__device__ __forceinline__ void publish(const Args<T>& a, const fwh::Task& k) {
+  st_release(a.ver + (size_t)k.ti * a.R + k.tj, k.r + 1);
+  if (k.type == 1 || k.type == 2) red_release_add(a.ctr + 1, 1u);
+  if (k.type == 3) red_release_add(a.ctr + 2, 1u);
+}
+
+// Optional per-task trace (sampled tasks): 10 words per entry.
+//   [0] task | type << 32   [1] SM id
+//   producer: [2] claimed  [3] inputs ready  [4] copies issued  [5] published
+//   compute : [6] descriptor seen  [9] task finished (stores issued)   [7], [8] unused
+__device__ __forceinline__ uint64_t* trace_slot(uint64_t* tr, int cap, int stride, int t) {
+  if (!tr || t < 0 || stride <= 0 || t % stride) return nullptr;
+  const int s = t / stride;
+  return s < cap ? tr + (size_t)s * 10 : nullptr;
+}
+__device__ __forceinline__ unsigned smid() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%smid;" : "=r"(r));
+  return r;
+}
+
+template <typename T, int BS>
+__global__ void __launch_bounds__(kWsThreads, 1) k_persistent_ws(Args<T> a) {
+  using L = WsLayout<BS>;
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ WsBars wb;
+  __shared__ CtaScratch cs;
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&wb.desc_full[i], 1);
+      mbar_init(&wb.desc_empty[i], kThreads / 32);
+      mbar_init(&wb.chunk_full[i], 1);
+      mbar_init(&wb.chunk_empty[i], kThreads / 32);
+    }
+    mbar_init(&wb.d_full, 1);
+    mbar_init(&wb.d_empty, kThreads / 32);
+    mbar_init(&wb.p_full, 1);
+    mbar_init(&wb.p_empty, kThreads / 32);
+    mbar_init(&wb.task_done, kThreads / 32);
+    for (int i = 0; i < kPubDepth; ++i) {
+      mbar_init(&wb.pub_full[i], 1);
+      mbar_init(&wb.pub_empty[i], 1);
+    }
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  if (warp == kThreads / 32 + 1) {
+    // ----------------------------------------------------------- publisher
+    if (lane == 0) {
+      for (unsigned i = 0;; ++i) {
+        const unsigned q = i % kPubDepth, ph = (i / kPubDepth) & 1;
+        if (!mbar_wait(&wb.pub_full[q], ph, a.status, a.abort_flag, a.timeout_ns)) break;
+        const int t = wb.pubq[q][0];
+        const fwh::Task k{wb.pubq[q][1], wb.pubq[q][2], wb.pubq[q][3], wb.pubq[q][4]};
+        if (t < 0) break;
+        // tasks finish in hand-off order: the i-th completion is this task
+        if (!mbar_wait(&wb.task_done, i & 1, a.status, a.abort_flag, a.timeout_ns)) break;
+        if (t != a.skip_task) publish(a, k);
+        if (uint64_t* tr = trace_slot(a.trace, a.trace_cap, a.trace_stride, t)) tr[5] = globaltimer();
+        mbar_arrive(&wb.pub_empty[q]);
+      }
+    }
+    return;
+  }
+
+  if (warp == kThreads / 32) {
+    // ------------------------------------------------------------ producer
+    const int64_t total = a.stage_off[a.R + 1];
+    unsigned idesc = 0, ichunk = 0, jd = 0, jp = 0, ipub = 0;
+    auto no_idle = []() {};
+    for (;;) {
+      int t = -1;
+      if (lane == 0) {
+        const uint64_t tc = globaltimer();
+        const int64_t tt = atomicAdd(a.ctr, 1u);
+        int ok = tt < total && !ld_relaxed(a.abort_flag);
+        if (ok) ok = wait_deps(a, fwh::decode_task(tt, a.R, a.lookahead, a.stage_off), no_idle);
+        t = ok ? (int)tt : -1;
+        if (uint64_t* tr = trace_slot(a.trace, a.trace_cap, a.trace_stride, t)) {
+          tr[1] = smid();
+          tr[2] = tc;
+          tr[3] = globaltimer();
+        }
+      }
+      t = __shfl_sync(0xffffffffu, t, 0);
+      fwh::Task k{0, 0, 0, 0};
+      bool fast = false;
+      if (t >= 0) {
+        k = fwh::decode_task(t, a.R, a.lookahead, a.stage_off);
+        if (k.type == 3 && Num<T>::kInt && a.packed) {
+          const int slot = k.r & 1;
+          const int ba = __ldcg(a.colB + (size_t)slot * a.slot_tiles + k.ti);
+          const int bb = __ldcg(a.rowB + (size_t)slot * a.slot_tiles + k.tj);
+          fast = ba + bb < Keys<BS>::CAP;
+        }
+      }
+      unsigned pq = 0;
+      if (lane == 0) {
+        // queue the task for publication, then hand it to the compute warps
+        pq = ipub % kPubDepth;
+        mbar_wait(&wb.pub_empty[pq], ((ipub / kPubDepth) & 1) ^ 1, a.status, a.abort_flag,
+                  a.timeout_ns);
+        wb.pubq[pq][0] = t;
+        wb.pubq[pq][1] = k.type;
+        wb.pubq[pq][2] = k.r;
+        wb.pubq[pq][3] = k.ti;
+        wb.pubq[pq][4] = k.tj;
+        mbar_arrive(&wb.pub_full[pq]);
+        const unsigned ds = idesc & 1;
+        mbar_wait(&wb.desc_empty[ds], ((idesc >> 1) & 1) ^ 1, a.status, a.abort_flag,
+                  a.timeout_ns);
+        wb.desc[ds][0] = t;
+        wb.desc[ds][1] = k.type;
+        wb.desc[ds][2] = k.r;
+        wb.desc[ds][3] = k.ti;
+        wb.desc[ds][4] = k.tj;
+        wb.desc[ds][5] = fast ? 1 : 0;
+        mbar_arrive(&wb.desc_full[ds]);
+      }
+      ++idesc;
+      ++ipub;
+      if (t < 0) break;
+      if (k.type == 3) {
+        fence_proxy_async();  // global data published by other CTAs, read by TMA below
+        const int slot = k.r & 1;
+        // the tile's own D block, one bulk copy per valid row
+        const int64_t row0 = (int64_t)k.ti * BS, col0 = (int64_t)k.tj * BS;
+        const int nrows = (int)(a.n - row0 < (int64_t)BS ? a.n - row0 : (int64_t)BS);
+        const int ncols = (int)(a.n - col0 < (int64_t)BS ? a.n - col0 : (int64_t)BS);
+        const unsigned rowbytes = (unsigned)(((ncols + 3) / 4) * 4) * 4u;
+        if (lane == 0) {
+          mbar_wait(&wb.d_empty, (jd & 1) ^ 1, a.status, a.abort_flag, a.timeout_ns);
+          mbar_expect_tx(&wb.d_full, rowbytes * (unsigned)nrows);
+        }
+        __syncwarp();
+        unsigned char* dbuf = smem + L::d_off();
+        for (int rr = lane; rr < nrows; rr += 32)
+          bulk_g2s(dbuf + (size_t)rr * BS * sizeof(T), a.D + (row0 + rr) * a.ld + col0, rowbytes,
+                   &wb.d_full);
+        ++jd;
+        // operand chunks
+        const size_t toffA = ((size_t)slot * a.slot_tiles + k.ti) * BS * BS;
+        const size_t toffB = ((size_t)slot * a.slot_tiles + k.tj) * BS * BS;
+        const unsigned char* srcA = fast ? (const unsigned char*)(a.colK + toffA)
+                                         : (const unsigned char*)(a.colR + toffA);
+        const unsigned char* srcB = fast ? (const unsigned char*)(a.rowK + toffB)
+                                         : (const unsigned char*)(a.rowR + toffB);
+        for (int c = 0; c < L::NC; ++c) {
+          if (lane == 0) {
+            const unsigned st = ichunk & 1;
+            mbar_wait(&wb.chunk_empty[st], ((ichunk >> 1) & 1) ^ 1, a.status, a.abort_flag,
+                      a.timeout_ns);
+            mbar_expect_tx(&wb.chunk_full[st], 2 * (unsigned)L::kChunkBytes);
+            unsigned char* dst = smem + L::ring_off() + st * L::kStage;
+            bulk_g2s(dst, srcA + c * L::kChunkBytes, (unsigned)L::kChunkBytes, &wb.chunk_full[st]);
+            bulk_g2s(dst + L::kChunkBytes, srcB + c * L::kChunkBytes, (unsigned)L::kChunkBytes,
+                     &wb.chunk_full[st]);
+          }
+          ++ichunk;
+        }
+        // predecessor tile of the row panel snapshot
+        if (lane == 0) {
+          mbar_wait(&wb.p_empty, (jp & 1) ^ 1, a.status, a.abort_flag, a.timeout_ns);
+          mbar_expect_tx(&wb.p_full, (unsigned)L::kTile);
+          bulk_g2s(smem + L::p_off(), a.rowP + toffB, (unsigned)L::kTile, &wb.p_full);
+        }
+        ++jp;
+      } else if (lane == 0) {
+        // pivot / panel tasks use the ring and Dbuf as scratch: wait until this
+        // task has been published (its publication-queue slot frees up)
+        mbar_wait(&wb.pub_empty[pq], (((ipub - 1) / kPubDepth) & 1), a.status, a.abort_flag,
+                  a.timeout_ns);
+      }
+      if (lane == 0) {
+        if (uint64_t* tr = trace_slot(a.trace, a.trace_cap, a.trace_stride, t)) {
+          tr[0] = (uint64_t)(unsigned)t | ((uint64_t)k.type << 32);
+          tr[4] = globaltimer();
+        }
+      }
+      if (k.type != 3) fence_proxy_async();
+      __syncwarp();
+    }
+    // leave no bulk copy in flight: wait (bounded) for the last phase armed on
+    // every full barrier
+    if (lane == 0) {
+      if (jd) mbar_wait(&wb.d_full, (jd - 1) & 1, a.status, a.abort_flag, a.timeout_ns);
+      if (jp) mbar_wait(&wb.p_full, (jp - 1) & 1, a.status, a.abort_flag, a.timeout_ns);
+      for (unsigned c = ichunk >= 2 ? ichunk - 2 : 0; c < ichunk; ++c)
+        mbar_wait(&wb.chunk_full[c & 1], (c >> 1) & 1, a.status, a.abort_flag, a.timeout_ns);
+    }
+    return;
+  }
+
+  // -------------------------------------------------------------- compute
+  const TileCtx<T> ctx{a.D, a.P, a.n, a.ld, a.status, a.abort_flag, a.timeout_ns};
+  unsigned idesc = 0, dcnt = 0, ccnt = 0, pcnt = 0;
+  for (;;) {
+    const unsigned ds = idesc & 1;
+    if (!mbar_wait(&wb.desc_full[ds], (idesc >> 1) & 1, a.status, a.abort_flag, a.timeout_ns))
+      break;
+    const int t = wb.desc[ds][0];
+    const fwh::Task k{wb.desc[ds][1], wb.desc[ds][2], wb.desc[ds][3], wb.desc[ds][4]};
+    const bool fast = wb.desc[ds][5] != 0;
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&wb.desc_empty[ds]);
+    ++idesc;
+    if (t < 0) break;
+    uint64_t* tr = tid == 0 ? trace_slot(a.trace, a.trace_cap, a.trace_stride, t) : nullptr;
+    if (tr) tr[6] = globaltimer();
+    bool ok = true;
+    if (k.type == 3) {
+      ok = ws_minplus<T, BS>(ctx, k.ti, k.tj, fast, smem, &wb, dcnt, ccnt, pcnt);
+    } else if (k.type == 0) {
+      task_pivot<T, BS>(a, k.r, smem + L::ring_off(), &cs);
+      bar_compute();
+    } else {
+      // panel tasks put A in the ring region and B in Dbuf: contiguous, As + BS*BS = Dbuf
+      task_panel<T, BS>(a, k.r, k.type == 1 ? k.tj : k.ti, k.type == 1,
+                        smem + L::d_off() - (size_t)BS * BS * 4, &cs);
+      bar_compute();
+    }
+    if (tr) tr[9] = globaltimer();
+    if (!ok) break;
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&wb.task_done);
+  }
+}
+
+}  // namespace fwk
