@@ -99,11 +99,13 @@ def load():
         lib.fw_verify_certificate.argtypes = [P, P, P, I64, I64, P, P]
         lib.fw_queue_tasks.argtypes = [I32, I64, I64, I64, P]
         lib.fw_solve_noalloc.argtypes = [P, P, I64, I64, I32, P]
+        lib.fw_bs_table.argtypes = [P, I32]
+        lib.fw_autotune_bs.argtypes = [I32, I64, I64, P, P, P]
         for name in ("fw_solve", "fw_solve_ex", "fw_solve_host", "fw_batched_plan_create",
                      "fw_solve_batched", "fw_batched_plan_info", "fw_batched_plan_destroy",
                      "fw_backward", "fw_backward_strided", "fw_sync_status",
                      "fw_release_workspace", "fw_peak_probe", "fw_verify_certificate",
-                     "fw_queue_tasks", "fw_solve_noalloc"):
+                     "fw_queue_tasks", "fw_solve_noalloc", "fw_bs_table", "fw_autotune_bs"):
             getattr(lib, name).restype = I32
         _lib = lib
         return lib
@@ -230,11 +232,96 @@ def fw_queue_tasks(R: int, lookahead: int, first: int = 0, count: int | None = N
     return out
 
 
+class BatchedPlan:
+    """fw_batched_plan_create / fw_solve_batched / fw_batched_plan_destroy."""
+
+    def __init__(self, ns, lds, dtype: int = FW_I32, options: Options | None = None):
+        lib = load()
+        ns = np.ascontiguousarray(np.asarray(ns, np.int64))
+        lds = np.ascontiguousarray(np.asarray(lds, np.int64))
+        if ns.shape != lds.shape or ns.ndim != 1:
+            raise ValueError("ns and lds must be 1-D of equal length")
+        self.batch = len(ns)
+        self._h = ctypes.c_void_p()
+        o = ctypes.byref(options) if options is not None else None
+        check(lib.fw_batched_plan_create(ctypes.byref(self._h), ns.ctypes.data, lds.ctypes.data,
+                                         self.batch, dtype, o), "fw_batched_plan_create")
+        self._dp = (ctypes.c_void_p * self.batch)()
+        self._pp = (ctypes.c_void_p * self.batch)()
+
+    def solve(self, dists, preds, stream=None) -> None:
+        """dists/preds: sequences of CUDA tensors (n_b x n_b views) or raw device pointers."""
+        if len(dists) != self.batch or len(preds) != self.batch:
+            raise ValueError("expected %d graphs" % self.batch)
+        for b, (d, p) in enumerate(zip(dists, preds)):
+            self._dp[b] = d if isinstance(d, int) else d.data_ptr()
+            self._pp[b] = p if isinstance(p, int) else p.data_ptr()
+        check(load().fw_solve_batched(self._h, self._dp, self._pp, _stream_ptr(stream)),
+              "fw_solve_batched")
+
+    def info(self):
+        bs = np.zeros(self.batch, np.int32)
+        tot = ctypes.c_int64()
+        check(load().fw_batched_plan_info(self._h, bs.ctypes.data, ctypes.byref(tot)),
+              "fw_batched_plan_info")
+        return bs, tot.value
+
+    def close(self) -> None:
+        if self._h:
+            load().fw_batched_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def fw_bs_table(table=None) -> np.ndarray:
+    """Read (table=None) or set the 7-entry per-size-class block-size table."""
+    t = np.zeros(7, np.int32) if table is None else np.ascontiguousarray(table, np.int32)
+    check(load().fw_bs_table(t.ctypes.data, 0 if table is None else 1), "fw_bs_table")
+    return t
+
+
+def fw_autotune_bs(dtype: int = FW_I32, graphs_per_class: int = 32, max_n: int = 2048,
+                   stream=None):
+    """Measure and install the per-size-class block sizes; returns (table, best ms)."""
+    t = np.zeros(7, np.int32)
+    ms = np.zeros(7, np.float64)
+    check(load().fw_autotune_bs(dtype, graphs_per_class, max_n, _stream_ptr(stream),
+                                t.ctypes.data, ms.ctypes.data), "fw_autotune_bs")
+    return t, ms
+
+
 # ------------------------------------------------------------ convenience ---
 
 def padded(n: int) -> int:
     """Smallest leading dimension >= n that keeps rows 16-byte aligned."""
     return (n + 3) // 4 * 4
+
+
+def solve_batched(Ws, options: Options | None = None, stream=None, sync: bool = True):
+    """Out-of-place batched solve of CUDA weight matrices: returns [(D, P), ...]."""
+    import torch
+    Ds, Ps, ns, lds = [], [], [], []
+    for W in Ws:
+        n = W.shape[0]
+        ld = padded(n)
+        Dbuf = torch.empty((n, ld), dtype=W.dtype, device=W.device)
+        Pbuf = torch.empty((n, ld), dtype=torch.int32, device=W.device)
+        Dbuf[:, :n].copy_(W)
+        Ds.append(Dbuf[:, :n])
+        Ps.append(Pbuf[:, :n])
+        ns.append(n)
+        lds.append(ld)
+    plan = BatchedPlan(ns, lds, _dtype_code(Ws[0]), options)
+    plan.solve(Ds, Ps, stream)
+    if sync:
+        fw_sync_status(stream)
+    plan.close()
+    return list(zip(Ds, Ps))
 
 
 def solve(W, options: Options | None = None, stream=None, sync: bool = True):

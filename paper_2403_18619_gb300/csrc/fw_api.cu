@@ -178,6 +178,14 @@ fw_status solve_device(void* dist, int32_t* pred, int64_t n, int64_t ld, fw_dtyp
   return e == cudaSuccess ? FW_OK : FW_ERR_CUDA;
 }
 
+// Status word of (current device, stream), created if the stream has none yet.
+int* status_word_for(cudaStream_t s) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  StreamWs* w = nullptr;
+  if (get_ws(s, 0, &w) != FW_OK) return nullptr;
+  return w->status;
+}
+
 // Status word of (current device, stream); nullptr if the stream never solved.
 int* stream_status(cudaStream_t s) {
   int dev = 0;

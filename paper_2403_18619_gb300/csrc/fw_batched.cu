@@ -1,0 +1,580 @@
+// Batched solve: many independent graphs of different sizes in one persistent
+// launch, replayed from a CUDA graph.
+//
+// Every graph keeps its own blocked-FW task queue (decode_task with its own R,
+// block size and lookahead) and its own flags and snapshots.  The plan
+// interleaves the graphs' queues into one global list in "stage waves": stage
+// 0 of every graph, then stage 1 of every graph, ... (largest graphs first).
+// Each graph's tasks keep their relative order, so the global list is still a
+// topological order of every graph's dependencies, and a small graph's
+// latency-bound pivot chain hides behind other graphs' min-plus work.  One
+// kernel (the warp-specialised engine with a runtime block size per task)
+// drains the list.
+//
+// The block size of each graph comes from a per-size-class table, filled with
+// defaults or measured by fw_autotune_bs on this GPU.
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <numeric>
+#include <vector>
+
+#include "fw_ws.cuh"
+
+namespace fwk {
+
+template <typename T>
+struct BatchParams {
+  const Args<T>* graphs;
+  const int* bsv;
+  const uint2* list;  // (graph, task index within the graph's queue)
+  int64_t ntasks;
+  unsigned* next;
+  int* status;
+  int* abort_flag;
+  int64_t timeout_ns;
+};
+
+template <typename T>
+struct BatchSrc {
+  const Args<T>* graphs;
+  const int* bsv;
+  const uint2* list;
+  int64_t ntasks;
+  unsigned* next;
+  int* status;
+  int* abort_flag;
+  int64_t timeout_ns;
+  int skip_task = -1;
+  uint64_t* trace = nullptr;
+  int trace_cap = 0, trace_stride = 0;
+  __device__ explicit BatchSrc(const BatchParams<T>& p)
+      : graphs(p.graphs), bsv(p.bsv), list(p.list), ntasks(p.ntasks), next(p.next),
+        status(p.status), abort_flag(p.abort_flag), timeout_ns(p.timeout_ns) {}
+  __device__ int64_t total() const { return ntasks; }
+  __device__ fwh::Task resolve(int64_t t, int& g) const {
+    const uint2 e = list[t];
+    g = (int)e.x;
+    const Args<T>& a = graphs[g];
+    return fwh::decode_task((int64_t)e.y, a.R, a.lookahead, a.stage_off);
+  }
+  __device__ const Args<T>& args(int g) const { return graphs[g]; }
+  __device__ int bs(int g) const { return bsv[g]; }
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kWsThreads, 1) k_batched_ws(BatchParams<T> p) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ WsBars wb;
+  __shared__ CtaScratch cs;
+  const BatchSrc<T> src(p);
+  ws_engine<T, 0, 128>(src, smem, wb, cs);
+}
+
+// pred initialisation of every graph: blockIdx.y is the graph.
+template <typename T>
+__global__ void __launch_bounds__(256) k_batched_init(const Args<T>* graphs) {
+  const Args<T> a = graphs[blockIdx.y];
+  const int64_t total = a.n * a.n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / a.n, j = e - i * a.n;
+    const T w = a.D[i * a.ld + j];
+    a.P[i * a.ld + j] = (i != j && Num<T>::finite(w)) ? (int32_t)i : -1;
+  }
+}
+
+}  // namespace fwk
+
+namespace fwh {
+
+// ----------------------------------------------------------- size classes ----
+
+namespace {
+
+constexpr int kClasses = 7;  // n <= 128, 256, 512, 1024, 2048, 4096, larger
+const int64_t kClassMax[kClasses] = {128, 256, 512, 1024, 2048, 4096, 1 << 30};
+
+std::mutex g_table_mu;
+int g_bs_table[kClasses] = {32, 32, 64, 64, 128, 128, 128};
+
+int class_of(int64_t n) {
+  for (int c = 0; c < kClasses; ++c)
+    if (n <= kClassMax[c]) return c;
+  return kClasses - 1;
+}
+
+int table_bs(int64_t n) {
+  std::lock_guard<std::mutex> lk(g_table_mu);
+  return g_bs_table[class_of(n)];
+}
+
+constexpr size_t kAl = 256;
+size_t al(size_t x) { return (x + kAl - 1) / kAl * kAl; }
+
+}  // namespace
+
+}  // namespace fwh
+
+// ------------------------------------------------------------------ plan ----
+
+struct fw_batched_plan {
+  int device = 0;
+  fw_dtype dtype = FW_I32;
+  fw_options opt{};
+  int64_t batch = 0;
+  std::vector<int64_t> n, ld;
+  std::vector<int> bs, R;
+  void* dmem = nullptr;  // every device table and workspace of the plan
+  size_t dbytes = 0;
+  void* d_args = nullptr;
+  int* d_bs = nullptr;
+  uint2* d_list = nullptr;
+  int64_t ntasks = 0;
+  unsigned* d_next = nullptr;  // claim counter
+  int* d_abort = nullptr;
+  size_t flags_bytes = 0;      // the contiguous region zeroed before each solve
+  void* d_flags = nullptr;
+  std::vector<unsigned char> h_args;  // host copy of the per-graph Args
+  size_t args_size = 0;
+  std::vector<void*> cur_dist, cur_pred;
+  int* cur_status = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int grid = 0;
+  std::mutex mu;
+};
+
+namespace fwh {
+
+int* status_word_for(cudaStream_t s);  // fw_api.cu
+
+namespace {
+
+template <typename T>
+fw_status plan_build(fw_batched_plan* p) {
+  using A = fwk::Args<T>;
+  const int64_t B = p->batch;
+  p->args_size = sizeof(A);
+  // per-graph workspace sizes
+  std::vector<size_t> ws_bytes(B), flag_off(B), ws_off(B);
+  size_t flags = 0;
+  for (int64_t g = 0; g < B; ++g) {
+    flag_off[g] = flags;
+    flags += al((size_t)p->R[g] * p->R[g] * 4 + 4 * 4);  // ver + ctr
+  }
+  flags += al(4 * 4);  // next counter + abort
+  p->flags_bytes = flags;
+  size_t off = al(flags);
+  // per-graph stage offsets + snapshots (solve_ws_bytes covers flags too; the
+  // flag part of that carve is simply unused)
+  for (int64_t g = 0; g < B; ++g) {
+    ws_off[g] = off;
+    ws_bytes[g] = solve_ws_bytes(p->R[g], p->bs[g]);
+    off += al(ws_bytes[g]);
+  }
+  // the global task list (stage waves, largest graphs first)
+  std::vector<int64_t> order(B);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int64_t x, int64_t y) { return p->n[x] > p->n[y]; });
+  std::vector<std::vector<unsigned>> offs(B);
+  int maxR = 0;
+  int64_t total = 0;
+  const int64_t look = 2 * (int64_t)num_sms();
+  for (int64_t g = 0; g < B; ++g) {
+    offs[g].resize(p->R[g] + 2);
+    fill_stage_offsets(p->R[g], look, offs[g].data());
+    maxR = std::max(maxR, p->R[g]);
+    total += (int64_t)p->R[g] * p->R[g] * p->R[g];
+  }
+  if (total >= (int64_t)1 << 31) return FW_ERR_UNSUPPORTED;
+  std::vector<uint2> list;
+  list.reserve(total);
+  for (int s = 0; s <= maxR; ++s)
+    for (int64_t oi = 0; oi < B; ++oi) {
+      const int64_t g = order[oi];
+      if (s > p->R[g]) continue;
+      for (unsigned t = offs[g][s]; t < offs[g][s + 1]; ++t) list.push_back(make_uint2((unsigned)g, t));
+    }
+  p->ntasks = (int64_t)list.size();
+  const size_t list_off = off;
+  off += al(list.size() * sizeof(uint2));
+  const size_t args_off = off;
+  off += al((size_t)B * sizeof(A));
+  const size_t bs_off = off;
+  off += al((size_t)B * 4);
+  p->dbytes = off + kAl;
+  if (cudaMalloc(&p->dmem, p->dbytes) != cudaSuccess) {
+    cudaGetLastError();
+    p->dmem = nullptr;
+    return FW_ERR_NOMEM;
+  }
+  char* base = reinterpret_cast<char*>(p->dmem);
+  p->d_flags = base;
+  p->d_next = reinterpret_cast<unsigned*>(base + flags - al(4 * 4));
+  p->d_abort = reinterpret_cast<int*>(p->d_next + 1);
+  p->d_list = reinterpret_cast<uint2*>(base + list_off);
+  p->d_args = base + args_off;
+  p->d_bs = reinterpret_cast<int*>(base + bs_off);
+
+  // host copies of every graph's Args (D / P / status patched at solve time)
+  p->h_args.assign((size_t)B * sizeof(A), 0);
+  A* ha = reinterpret_cast<A*>(p->h_args.data());
+  std::vector<unsigned> all_offs;
+  for (int64_t g = 0; g < B; ++g) {
+    SolveWs w = carve_solve_ws(base + ws_off[g], p->R[g], p->bs[g]);
+    A a{};
+    a.D = nullptr;
+    a.P = nullptr;
+    a.n = p->n[g];
+    a.ld = p->ld[g];
+    a.R = p->R[g];
+    a.slot_tiles = w.slot_tiles;
+    a.ver = reinterpret_cast<int*>(base + flag_off[g]);
+    a.ctr = reinterpret_cast<unsigned*>(a.ver + (size_t)p->R[g] * p->R[g]);
+    a.abort_flag = p->d_abort;
+    a.status = nullptr;
+    a.stage_off = w.stage_off;
+    a.lookahead = (int)look;
+    a.skip_task = -1;
+    a.timeout_ns = p->opt.timeout_ns > 0 ? p->opt.timeout_ns : 2000000000LL;
+    a.packed = p->opt.packed_keys ? 1 : 0;
+    a.piv = reinterpret_cast<T*>(w.piv);
+    a.pivP = w.pivP;
+    a.colK = w.colK;
+    a.colR = reinterpret_cast<T*>(w.colR);
+    a.colB = w.colB;
+    a.rowK = w.rowK;
+    a.rowR = reinterpret_cast<T*>(w.rowR);
+    a.rowP = w.rowP;
+    a.rowB = w.rowB;
+    a.trace = nullptr;
+    ha[g] = a;
+    if (cudaMemcpy(w.stage_off, offs[g].data(), offs[g].size() * 4, cudaMemcpyHostToDevice) !=
+        cudaSuccess)
+      return FW_ERR_CUDA;
+  }
+  if (cudaMemcpy(p->d_list, list.data(), list.size() * sizeof(uint2), cudaMemcpyHostToDevice) !=
+          cudaSuccess ||
+      cudaMemcpy(p->d_bs, p->bs.data(), (size_t)B * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+    return FW_ERR_CUDA;
+
+  const size_t smem = fwk::WsLayout<128>::bytes();
+  auto kern = fwk::k_batched_ws<T>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess)
+    return FW_ERR_CUDA;
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, fwk::kWsThreads, smem) !=
+          cudaSuccess ||
+      occ < 1)
+    return FW_ERR_CUDA;
+  int64_t grid = (int64_t)occ * num_sms();
+  if (p->opt.grid > 0 && p->opt.grid < grid) grid = p->opt.grid;
+  if (grid > p->ntasks) grid = p->ntasks;
+  p->grid = (int)std::max<int64_t>(grid, 1);
+  return FW_OK;
+}
+
+// Enqueue (or capture) the work of one batched solve on stream s.
+template <typename T>
+cudaError_t enqueue(fw_batched_plan* p, cudaStream_t s) {
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(p->d_flags, 0, p->flags_bytes, s)) != cudaSuccess) return e;
+  int64_t maxn2 = 0;
+  for (int64_t g = 0; g < p->batch; ++g) maxn2 = std::max(maxn2, p->n[g] * p->n[g]);
+  const unsigned gx = (unsigned)std::min<int64_t>((maxn2 + 255) / 256, 64);
+  const auto* args = reinterpret_cast<const fwk::Args<T>*>(p->d_args);
+  for (int64_t g0 = 0; g0 < p->batch; g0 += 65535) {
+    const unsigned gy = (unsigned)std::min<int64_t>(p->batch - g0, 65535);
+    fwk::k_batched_init<T><<<dim3(gx, gy), 256, 0, s>>>(args + g0);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  fwk::BatchParams<T> bp;
+  bp.graphs = args;
+  bp.bsv = p->d_bs;
+  bp.list = p->d_list;
+  bp.ntasks = p->ntasks;
+  bp.next = p->d_next;
+  bp.status = p->cur_status;
+  bp.abort_flag = p->d_abort;
+  bp.timeout_ns = p->opt.timeout_ns > 0 ? p->opt.timeout_ns : 2000000000LL;
+  cudaLaunchConfig_t lc{};
+  lc.gridDim = dim3((unsigned)p->grid);
+  lc.blockDim = dim3(fwk::kWsThreads);
+  lc.dynamicSmemBytes = fwk::WsLayout<128>::bytes();
+  lc.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  lc.attrs = attr;
+  lc.numAttrs = 1;
+  return cudaLaunchKernelEx(&lc, fwk::k_batched_ws<T>, bp);
+}
+
+template <typename T>
+fw_status solve_plan(fw_batched_plan* p, void* const* dist, int32_t* const* pred,
+                     cudaStream_t s) {
+  using A = fwk::Args<T>;
+  int* st = status_word_for(s);
+  if (!st) return FW_ERR_NOMEM;
+  bool changed = st != p->cur_status;
+  for (int64_t g = 0; g < p->batch && !changed; ++g)
+    changed = dist[g] != p->cur_dist[g] || (void*)pred[g] != p->cur_pred[g];
+  if (changed) {
+    // new buffers: refresh the device tables, then re-record the graph
+    if (cudaStreamSynchronize(s) != cudaSuccess) return FW_ERR_CUDA;
+    A* ha = reinterpret_cast<A*>(p->h_args.data());
+    for (int64_t g = 0; g < p->batch; ++g) {
+      ha[g].D = reinterpret_cast<T*>(dist[g]);
+      ha[g].P = pred[g];
+      ha[g].status = st;
+      p->cur_dist[g] = dist[g];
+      p->cur_pred[g] = pred[g];
+    }
+    p->cur_status = st;
+    if (cudaMemcpy(p->d_args, p->h_args.data(), p->h_args.size(), cudaMemcpyHostToDevice) !=
+        cudaSuccess)
+      return FW_ERR_CUDA;
+    if (p->exec) {
+      cudaGraphExecDestroy(p->exec);
+      p->exec = nullptr;
+    }
+    if (p->graph) {
+      cudaGraphDestroy(p->graph);
+      p->graph = nullptr;
+    }
+  }
+  if (!p->exec) {
+    if (!p->cap_stream &&
+        cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+      return FW_ERR_CUDA;
+    if (cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+      return FW_ERR_CUDA;
+    const cudaError_t e = enqueue<T>(p, p->cap_stream);
+    cudaGraph_t gr = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(p->cap_stream, &gr);
+    if (e != cudaSuccess || e2 != cudaSuccess || !gr) {
+      if (gr) cudaGraphDestroy(gr);
+      cudaGetLastError();
+      return FW_ERR_CUDA;
+    }
+    p->graph = gr;
+    if (cudaGraphInstantiate(&p->exec, gr, 0) != cudaSuccess) {
+      cudaGetLastError();
+      p->exec = nullptr;
+      return FW_ERR_CUDA;
+    }
+  }
+  if (p->opt.ev_start) cudaEventRecord(reinterpret_cast<cudaEvent_t>(p->opt.ev_start), s);
+  if (cudaGraphLaunch(p->exec, s) != cudaSuccess) return FW_ERR_CUDA;
+  if (p->opt.ev_stop) cudaEventRecord(reinterpret_cast<cudaEvent_t>(p->opt.ev_stop), s);
+  return FW_OK;
+}
+
+void plan_free(fw_batched_plan* p) {
+  if (p->exec) cudaGraphExecDestroy(p->exec);
+  if (p->graph) cudaGraphDestroy(p->graph);
+  if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+  if (p->dmem) cudaFree(p->dmem);
+  p->exec = nullptr;
+  p->graph = nullptr;
+  p->cap_stream = nullptr;
+  p->dmem = nullptr;
+}
+
+// ------------------------------------------------------------- autotuning ----
+
+// Timing workload of the autotuner (any valid graph will do): a dense digraph
+// with int32 weights in [1, 100] (or fp32 in (0, 1]) from a hash of (g, i, j).
+template <typename T>
+__global__ void k_tune_fill(T* D, int64_t n, int64_t ld, int g) {
+  const int64_t total = n * n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / n, j = e - i * n;
+    uint32_t h = (uint32_t)(i * 73856093u) ^ (uint32_t)(j * 19349663u) ^ (uint32_t)(g * 83492791u);
+    h ^= h >> 13;
+    h *= 0x5bd1e995u;
+    h ^= h >> 15;
+    T v;
+    if (i == j) v = T(0);
+    else if ((h & 7u) < 3u) v = fwk::Num<T>::inf();  // ~37% missing edges
+    else if constexpr (fwk::Num<T>::kInt) v = (T)(1 + (h >> 8) % 100);
+    else v = (T)(((h >> 8) & 0xffffu) + 1) * (1.0f / 65536.0f);
+    D[i * ld + j] = v;
+  }
+}
+
+}  // namespace
+}  // namespace fwh
+
+using namespace fwh;
+
+extern "C" {
+
+fw_status fw_batched_plan_create(fw_batched_plan** plan, const int64_t* n, const int64_t* ld,
+                                 int64_t batch, fw_dtype dtype, const fw_options* opt) {
+  if (!plan) return FW_ERR_ARG;
+  *plan = nullptr;
+  if (!n || !ld || batch < 1 || batch > 65536) return FW_ERR_ARG;
+  if (dtype != FW_I32 && dtype != FW_F32) return FW_ERR_ARG;
+  fw_options o;
+  fw_options_default(&o);
+  if (opt) o = *opt;
+  if (o.bs != 0 && o.bs != 32 && o.bs != 64 && o.bs != 128) return FW_ERR_ARG;
+  for (int64_t g = 0; g < batch; ++g)
+    if (n[g] < 1 || n[g] > 131072 || ld[g] < n[g] || (ld[g] % 4) != 0) return FW_ERR_ARG;
+  auto* p = new fw_batched_plan();
+  cudaGetDevice(&p->device);
+  p->dtype = dtype;
+  p->opt = o;
+  p->batch = batch;
+  p->n.assign(n, n + batch);
+  p->ld.assign(ld, ld + batch);
+  p->bs.resize(batch);
+  p->R.resize(batch);
+  for (int64_t g = 0; g < batch; ++g) {
+    p->bs[g] = o.bs ? o.bs : table_bs(n[g]);
+    p->R[g] = (int)((n[g] + p->bs[g] - 1) / p->bs[g]);
+    if (p->R[g] > 1024) {
+      delete p;
+      return FW_ERR_UNSUPPORTED;
+    }
+  }
+  p->cur_dist.assign(batch, nullptr);
+  p->cur_pred.assign(batch, nullptr);
+  const fw_status st = dtype == FW_I32 ? plan_build<int32_t>(p) : plan_build<float>(p);
+  if (st != FW_OK) {
+    plan_free(p);
+    delete p;
+    return st;
+  }
+  *plan = p;
+  return FW_OK;
+}
+
+fw_status fw_solve_batched(fw_batched_plan* p, void* const* dist, int32_t* const* pred,
+                           void* stream) {
+  if (!p || !dist || !pred) return FW_ERR_ARG;
+  for (int64_t g = 0; g < p->batch; ++g) {
+    if (!dist[g] || !pred[g] || dist[g] == (void*)pred[g]) return FW_ERR_ARG;
+    if ((reinterpret_cast<uintptr_t>(dist[g]) & 15) || (reinterpret_cast<uintptr_t>(pred[g]) & 15))
+      return FW_ERR_ARG;
+  }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != p->device) return FW_ERR_ARG;
+  std::lock_guard<std::mutex> lk(p->mu);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  return p->dtype == FW_I32 ? solve_plan<int32_t>(p, dist, pred, s)
+                            : solve_plan<float>(p, dist, pred, s);
+}
+
+fw_status fw_batched_plan_info(const fw_batched_plan* p, int32_t* bs_per_graph,
+                               int64_t* total_tasks) {
+  if (!p) return FW_ERR_ARG;
+  if (bs_per_graph)
+    for (int64_t g = 0; g < p->batch; ++g) bs_per_graph[g] = p->bs[g];
+  if (total_tasks) *total_tasks = p->ntasks;
+  return FW_OK;
+}
+
+fw_status fw_batched_plan_destroy(fw_batched_plan* p) {
+  if (!p) return FW_OK;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev != p->device) cudaSetDevice(p->device);
+  cudaDeviceSynchronize();
+  plan_free(p);
+  if (dev != p->device) cudaSetDevice(dev);
+  delete p;
+  return FW_OK;
+}
+
+fw_status fw_bs_table(int32_t* table, int32_t set) {
+  if (!table) return FW_ERR_ARG;
+  std::lock_guard<std::mutex> lk(g_table_mu);
+  if (set) {
+    for (int c = 0; c < kClasses; ++c)
+      if (table[c] != 32 && table[c] != 64 && table[c] != 128) return FW_ERR_ARG;
+    for (int c = 0; c < kClasses; ++c) g_bs_table[c] = table[c];
+  } else {
+    for (int c = 0; c < kClasses; ++c) table[c] = g_bs_table[c];
+  }
+  return FW_OK;
+}
+
+fw_status fw_autotune_bs(fw_dtype dtype, int64_t graphs_per_class, int64_t max_n, void* stream,
+                         int32_t* table_out, double* ms_out) {
+  if (dtype != FW_I32 && dtype != FW_F32) return FW_ERR_ARG;
+  if (graphs_per_class < 1 || graphs_per_class > 4096 || max_n < 1) return FW_ERR_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  int32_t table[kClasses];
+  fw_bs_table(table, 0);
+  const int cand[3] = {32, 64, 128};
+  for (int c = 0; c < kClasses; ++c) {
+    const int64_t n = std::min<int64_t>(c + 1 < kClasses ? kClassMax[c] : 8192, max_n);
+    if (c > 0 && n <= kClassMax[c - 1]) break;  // classes above max_n keep their entry
+    const int64_t ld = (n + 3) / 4 * 4;
+    const size_t bytes = (size_t)n * ld * 4;
+    std::vector<void*> dd(graphs_per_class), pp(graphs_per_class);
+    void* buf = nullptr;
+    if (cudaMalloc(&buf, bytes * 2 * graphs_per_class) != cudaSuccess) {
+      cudaGetLastError();
+      return FW_ERR_NOMEM;
+    }
+    std::vector<int64_t> ns(graphs_per_class, n), lds(graphs_per_class, ld);
+    for (int64_t g = 0; g < graphs_per_class; ++g) {
+      dd[g] = (char*)buf + 2 * g * bytes;
+      pp[g] = (char*)buf + (2 * g + 1) * bytes;
+    }
+    double best_ms = 1e30;
+    int best = table[c];
+    for (int bi = 0; bi < 3; ++bi) {
+      fw_options o;
+      fw_options_default(&o);
+      o.bs = cand[bi];
+      fw_batched_plan* plan = nullptr;
+      if (fw_batched_plan_create(&plan, ns.data(), lds.data(), graphs_per_class, dtype, &o) !=
+          FW_OK)
+        continue;
+      cudaEvent_t e0, e1;
+      cudaEventCreate(&e0);
+      cudaEventCreate(&e1);
+      float total = 0;
+      bool ok = true;
+      for (int rep = 0; rep < 3 && ok; ++rep) {
+        for (int64_t g = 0; g < graphs_per_class; ++g) {
+          if (dtype == FW_I32)
+            k_tune_fill<int32_t><<<64, 256, 0, s>>>((int32_t*)dd[g], n, ld, (int)g);
+          else
+            k_tune_fill<float><<<64, 256, 0, s>>>((float*)dd[g], n, ld, (int)g);
+        }
+        cudaEventRecord(e0, s);
+        ok = fw_solve_batched(plan, dd.data(), (int32_t* const*)pp.data(), stream) == FW_OK;
+        cudaEventRecord(e1, s);
+        ok = ok && fw_sync_status(stream) == FW_OK;
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0) total += ms;  // the first run records the graph
+      }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      fw_batched_plan_destroy(plan);
+      if (ok && total / 2 < best_ms) {
+        best_ms = total / 2;
+        best = cand[bi];
+      }
+    }
+    cudaFree(buf);
+    table[c] = best;
+    if (ms_out) ms_out[c] = best_ms;
+  }
+  fw_bs_table(table, 1);
+  if (table_out)
+    for (int c = 0; c < kClasses; ++c) table_out[c] = table[c];
+  return FW_OK;
+}
+
+}  // extern "C"

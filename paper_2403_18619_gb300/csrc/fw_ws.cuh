@@ -2,20 +2,26 @@
 // concurrency, Sec. 3.2, extended across rounds as the paper's future work
 // proposes, Sec. 5).
 //
-// A CTA has 8 compute warps, 1 producer warp and 1 publisher warp.  The
-// publisher sleeps on the compute warps' task-done barrier and publishes each
-// finished tile (the GPU-scope release), so that neither the compute warps nor
-// the producer wait on that fence.  The producer claims tasks
-// from the global queue in order, waits (bounded) on the tiles' ready flags,
-// and streams the operands of the remaining-tile tasks into shared memory with
-// TMA bulk copies while the compute warps work on the previous task:
-//   * the tile's own D block (one bulk copy per row)          -> Dbuf
-//   * the A and B panel snapshots, 32 k-steps per chunk       -> 2-stage ring
-//   * the predecessor tile of the B panel (for the epilogue)  -> Pbuf
-// mbarriers carry "full" (transaction bytes landed) and "empty" (compute
-// warps done reading) signals.  Pivot and panel tasks are run by the compute
-// warps alone (they use the ring and Dbuf as scratch); the producer waits for
-// them to finish before it touches shared memory again.
+// A CTA has 8 compute warps, 1 producer warp and 1 publisher warp.
+//   * The producer claims tasks from a global queue in order, waits (bounded)
+//     on the tiles' ready flags, and streams the operands of remaining-tile
+//     tasks into shared memory with TMA bulk copies while the compute warps
+//     work on the previous task:
+//       - the tile's own D block (one bulk copy per row)          -> Dbuf
+//       - the A and B panel snapshots, 32 k-steps per chunk       -> 2-stage ring
+//       - the predecessor tile of the B panel (for the epilogue)  -> Pbuf
+//   * The compute warps relax (min-plus over the chunks) and store improved
+//     entries; pivot and panel tasks are run by them alone, using the ring and
+//     Dbuf as scratch (the producer waits until such a task is published).
+//   * The publisher sleeps on the compute warps' task-done barrier and
+//     publishes each finished tile (the GPU-scope release), so that neither the
+//     compute warps nor the producer wait on that fence.
+// mbarriers carry "full" (transaction bytes landed) and "empty" (compute warps
+// done reading) signals.
+//
+// The same engine runs one graph (fw_solve) or a batch of graphs with
+// different sizes and block sizes in one launch (fw_solve_batched): a "task
+// source" maps a global queue index to (graph, task).
 #pragma once
 
 #include "fw_device.cuh"
@@ -28,15 +34,22 @@ namespace fwk {
 // thread (ptxas derives this from the launch bounds).
 constexpr int kWsThreads = kThreads + 64;
 constexpr int kPubDepth = 4;  // tasks handed to the compute warps but not yet published
-constexpr int kCK = 32;  // k-steps per streamed chunk
+constexpr int kCK = 32;       // k-steps per streamed chunk
 
+// Operand sizes of a task with block size BS.
 template <int BS>
-struct WsLayout {
-  static constexpr int NC = BS / kCK;                      // chunks per task
+struct WsChunk {
+  static constexpr int NC = BS / kCK;                          // chunks per task
   static constexpr size_t kChunkBytes = (size_t)kCK * BS * 4;  // one operand chunk
-  static constexpr size_t kStage = 2 * kChunkBytes;        // A chunk + B chunk
-  static constexpr size_t kRing = 2 * kStage;
   static constexpr size_t kTile = (size_t)BS * BS * 4;
+};
+
+// Shared-memory layout sized for the largest block size LBS a launch runs.
+template <int LBS>
+struct WsLayout {
+  static constexpr size_t kStage = 2 * WsChunk<LBS>::kChunkBytes;  // A chunk + B chunk
+  static constexpr size_t kRing = 2 * kStage;
+  static constexpr size_t kTile = WsChunk<LBS>::kTile;
   __host__ __device__ static constexpr size_t ring_off() { return 0; }
   __host__ __device__ static constexpr size_t d_off() { return kRing; }
   __host__ __device__ static constexpr size_t p_off() { return kRing + kTile; }
@@ -49,8 +62,8 @@ struct WsBars {
   uint64_t chunk_full[2], chunk_empty[2];
   uint64_t d_full, d_empty, p_full, p_empty, task_done;
   uint64_t pub_full[kPubDepth], pub_empty[kPubDepth];
-  int desc[2][8];           // t, type, r, ti, tj, fast
-  int pubq[kPubDepth][5];   // t, type, r, ti, tj of tasks awaiting publication
+  int desc[2][8];           // t, type, r, ti, tj, fast, graph
+  int pubq[kPubDepth][6];   // t, type, r, ti, tj, graph of tasks awaiting publication
 };
 
 // Bounded wait on an mbarrier phase; false (and the timeout status) on expiry.
@@ -78,15 +91,22 @@ struct TileCtx {
   int64_t timeout_ns;
 };
 
-// Compute-warp side of a remaining-tile task (phase 4 of round r, tile ti,tj).
-// Returns false if an operand never arrived (the kernel then stops).
-template <typename T, int BS>
+// Counters of the shared-memory pipelines (each side keeps its own copy).
+struct PipeCnt {
+  unsigned d = 0, chunk = 0, p = 0;
+};
+
+// ------------------------------------------------------------ compute side ----
+
+// Remaining-tile task (phase 4 of round r, tile ti,tj).  Returns false if an
+// operand never arrived (the kernel then stops).
+template <typename T, int BS, int LBS>
 __device__ __noinline__ bool ws_minplus(TileCtx<T> c, int ti, int tj, bool fast,
-                                        unsigned char* smem, WsBars* wb, unsigned& dcnt,
-                                        unsigned& ccnt, unsigned& pcnt) {
+                                        unsigned char* smem, WsBars* wb, PipeCnt& pc) {
   using Gm = Geo<BS>;
   using K = Keys<BS>;
-  using L = WsLayout<BS>;
+  using L = WsLayout<LBS>;
+  using C = WsChunk<BS>;
   constexpr int TM = Gm::TM, G = Gm::G;
   constexpr bool kInt = Num<T>::kInt;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4, lane = tid & 31;
@@ -98,7 +118,7 @@ __device__ __noinline__ bool ws_minplus(TileCtx<T> c, int ti, int tj, bool fast,
   const int ncol = (int)(c.n - col0 < BS ? c.n - col0 : BS);
 
   // 1. the tile's current values (rows/columns beyond n read as INF)
-  if (!mbar_wait(&wb->d_full, dcnt & 1, c.status, c.abort_flag, c.timeout_ns)) return false;
+  if (!mbar_wait(&wb->d_full, pc.d & 1, c.status, c.abort_flag, c.timeout_ns)) return false;
   T old[TM][TM];
 #pragma unroll
   for (int m = 0; m < TM; ++m) {
@@ -115,7 +135,7 @@ __device__ __noinline__ bool ws_minplus(TileCtx<T> c, int ti, int tj, bool fast,
   }
   __syncwarp();
   if (lane == 0) mbar_arrive(&wb->d_empty);
-  ++dcnt;
+  ++pc.d;
 
   T* Drow = c.D + row0 * c.ld + col0;
   int32_t* Prow = c.P + row0 * c.ld + col0;
@@ -126,18 +146,19 @@ __device__ __noinline__ bool ws_minplus(TileCtx<T> c, int ti, int tj, bool fast,
     for (int m = 0; m < TM; ++m)
 #pragma unroll
       for (int nn = 0; nn < TM; ++nn) acc[m][nn] = kInt ? key_of<BS>((int32_t)old[m][nn]) : 0u;
-    for (int ch = 0; ch < L::NC; ++ch) {
-      const unsigned st = ccnt & 1;
-      if (!mbar_wait(&wb->chunk_full[st], (ccnt >> 1) & 1, c.status, c.abort_flag, c.timeout_ns))
+    for (int ch = 0; ch < C::NC; ++ch) {
+      const unsigned st = pc.chunk & 1;
+      if (!mbar_wait(&wb->chunk_full[st], (pc.chunk >> 1) & 1, c.status, c.abort_flag,
+                     c.timeout_ns))
         return false;
       const uint32_t* As = reinterpret_cast<const uint32_t*>(ring + st * L::kStage);
       const uint32_t* Bs = As + kCK * BS;
       core_packed<BS, kCK>(As, Bs, acc, tx, ty);
       __syncwarp();
       if (lane == 0) mbar_arrive(&wb->chunk_empty[st]);
-      ++ccnt;
+      ++pc.chunk;
     }
-    if (!mbar_wait(&wb->p_full, pcnt & 1, c.status, c.abort_flag, c.timeout_ns)) return false;
+    if (!mbar_wait(&wb->p_full, pc.p & 1, c.status, c.abort_flag, c.timeout_ns)) return false;
 #pragma unroll
     for (int m = 0; m < TM; ++m) {
       const int lr = Gm::idx(ty, m);
@@ -159,18 +180,19 @@ __device__ __noinline__ bool ws_minplus(TileCtx<T> c, int ti, int tj, bool fast,
     for (int m = 0; m < TM; ++m)
 #pragma unroll
       for (int nn = 0; nn < TM; ++nn) arg[m][nn] = 0;
-    for (int ch = 0; ch < L::NC; ++ch) {
-      const unsigned st = ccnt & 1;
-      if (!mbar_wait(&wb->chunk_full[st], (ccnt >> 1) & 1, c.status, c.abort_flag, c.timeout_ns))
+    for (int ch = 0; ch < C::NC; ++ch) {
+      const unsigned st = pc.chunk & 1;
+      if (!mbar_wait(&wb->chunk_full[st], (pc.chunk >> 1) & 1, c.status, c.abort_flag,
+                     c.timeout_ns))
         return false;
       const T* As = reinterpret_cast<const T*>(ring + st * L::kStage);
       const T* Bs = As + kCK * BS;
       core_generic<BS, T, kCK>(As, Bs, old, arg, tx, ty, ch * kCK);
       __syncwarp();
       if (lane == 0) mbar_arrive(&wb->chunk_empty[st]);
-      ++ccnt;
+      ++pc.chunk;
     }
-    if (!mbar_wait(&wb->p_full, pcnt & 1, c.status, c.abort_flag, c.timeout_ns)) return false;
+    if (!mbar_wait(&wb->p_full, pc.p & 1, c.status, c.abort_flag, c.timeout_ns)) return false;
 #pragma unroll
     for (int m = 0; m < TM; ++m) {
       const int lr = Gm::idx(ty, m);
@@ -187,28 +209,44 @@ __device__ __noinline__ bool ws_minplus(TileCtx<T> c, int ti, int tj, bool fast,
   }
   __syncwarp();
   if (lane == 0) mbar_arrive(&wb->p_empty);
-  ++pcnt;
+  ++pc.p;
   if (neg) atomicOr(c.status, kStNegCycle);
   return true;
 }
 
-// ----------------------------------------------------- persistent driver ----
+// Any task, compute-warp side.
+template <typename T, int BS, int LBS>
+__device__ bool compute_task(const Args<T>& a, const fwh::Task& k, bool fast, unsigned char* smem,
+                             WsBars* wb, CtaScratch* cs, PipeCnt& pc) {
+  using L = WsLayout<LBS>;
+  if (k.type == 3) {
+    const TileCtx<T> ctx{a.D, a.P, a.n, a.ld, a.status, a.abort_flag, a.timeout_ns};
+    return ws_minplus<T, BS, LBS>(ctx, k.ti, k.tj, fast, smem, wb, pc);
+  }
+  if (k.type == 0) {
+    task_pivot<T, BS>(a, k.r, smem + L::ring_off(), cs);
+  } else {
+    // panel tasks put A in the ring region and B in Dbuf: contiguous, As + BS*BS = Dbuf
+    task_panel<T, BS>(a, k.r, k.type == 1 ? k.tj : k.ti, k.type == 1,
+                      smem + L::d_off() - (size_t)BS * BS * 4, cs);
+  }
+  bar_compute();
+  return true;
+}
 
-// Bounded wait until *p >= target (producer lane only).  `idle()` runs on
-// every poll (the producer publishes its previous task from there, so that a
-// task never waits on a task whose publication it is itself holding up).
-// Gives up when another CTA has aborted or when the wait exceeds timeout_ns;
-// then records the timeout and raises the abort flag so that every CTA stops.
-template <typename Idle>
+// ----------------------------------------------------------- producer side ----
+
+// Bounded wait until *p >= target (producer lane only).  Gives up when another
+// CTA has aborted or when the wait exceeds timeout_ns; then records the
+// timeout and raises the abort flag so that every CTA stops.
 __device__ __forceinline__ bool wait_ge(const int* p, int target, int* abort_flag, int* status,
-                                        int64_t timeout_ns, Idle&& idle) {
+                                        int64_t timeout_ns) {
   if (ld_acquire(p) >= target) return true;
   const uint64_t t0 = globaltimer();
   // iteration cap as well as the clock: each iteration sleeps >= 32 ns
   const int64_t max_it = timeout_ns / 32 + 1024;
   unsigned ns = 32;
   for (int64_t it = 0;; ++it) {
-    idle();
     __nanosleep(ns);
     if (ns < 256) ns <<= 1;
     if (ld_acquire(p) >= target) return true;
@@ -223,12 +261,12 @@ __device__ __forceinline__ bool wait_ge(const int* p, int target, int* abort_fla
 
 // Inputs of task k (Sec. 2.3.1 phase order, Opt-9's per-block dependencies of
 // Sec. 3.2, and the slot reuse of the double-buffered snapshots).
-template <typename T, typename Idle>
-__device__ bool wait_deps(const Args<T>& a, const fwh::Task& k, Idle&& idle) {
+template <typename T>
+__device__ bool wait_deps(const Args<T>& a, const fwh::Task& k) {
   const int R = a.R;
   const int* ver = a.ver;
   auto w = [&](const int* p, int target) {
-    return wait_ge(p, target, a.abort_flag, a.status, a.timeout_ns, idle);
+    return wait_ge(p, target, a.abort_flag, a.status, a.timeout_ns);
   };
   const int* done2 = reinterpret_cast<const int*>(a.ctr + 1);
   const int* done3 = reinterpret_cast<const int*>(a.ctr + 2);
@@ -262,13 +300,75 @@ __device__ __forceinline__ void publish(const Args<T>& a, const fwh::Task& k) {
   if (k.type == 3) red_release_add(a.ctr + 2, 1u);
 }
 
+// Whether a remaining-tile task may relax packed keys (int32, bounded panels).
+template <typename T, int BS>
+__device__ __forceinline__ bool packed_ok(const Args<T>& a, const fwh::Task& k) {
+  if (!(Num<T>::kInt && a.packed && k.type == 3)) return false;
+  const int slot = k.r & 1;
+  const int ba = __ldcg(a.colB + (size_t)slot * a.slot_tiles + k.ti);
+  const int bb = __ldcg(a.rowB + (size_t)slot * a.slot_tiles + k.tj);
+  return ba + bb < Keys<BS>::CAP;
+}
+
+// Issue the operand copies of remaining-tile task k (whole producer warp).
+template <typename T, int BS, int LBS>
+__device__ void issue_operands(const Args<T>& a, const fwh::Task& k, bool fast, unsigned char* smem,
+                               WsBars* wb, PipeCnt& pc, int lane) {
+  using L = WsLayout<LBS>;
+  using C = WsChunk<BS>;
+  fence_proxy_async();  // global data published by other CTAs, read by TMA below
+  const int slot = k.r & 1;
+  // the tile's own D block, one bulk copy per valid row
+  const int64_t row0 = (int64_t)k.ti * BS, col0 = (int64_t)k.tj * BS;
+  const int nrows = (int)(a.n - row0 < (int64_t)BS ? a.n - row0 : (int64_t)BS);
+  const int ncols = (int)(a.n - col0 < (int64_t)BS ? a.n - col0 : (int64_t)BS);
+  const unsigned rowbytes = (unsigned)(((ncols + 3) / 4) * 4) * 4u;
+  if (lane == 0) {
+    mbar_wait(&wb->d_empty, (pc.d & 1) ^ 1, a.status, a.abort_flag, a.timeout_ns);
+    mbar_expect_tx(&wb->d_full, rowbytes * (unsigned)nrows);
+  }
+  __syncwarp();
+  unsigned char* dbuf = smem + L::d_off();
+  for (int rr = lane; rr < nrows; rr += 32)
+    bulk_g2s(dbuf + (size_t)rr * BS * sizeof(T), a.D + (row0 + rr) * a.ld + col0, rowbytes,
+             &wb->d_full);
+  ++pc.d;
+  // operand chunks
+  const size_t toffA = ((size_t)slot * a.slot_tiles + k.ti) * BS * BS;
+  const size_t toffB = ((size_t)slot * a.slot_tiles + k.tj) * BS * BS;
+  const unsigned char* srcA = fast ? (const unsigned char*)(a.colK + toffA)
+                                   : (const unsigned char*)(a.colR + toffA);
+  const unsigned char* srcB = fast ? (const unsigned char*)(a.rowK + toffB)
+                                   : (const unsigned char*)(a.rowR + toffB);
+  for (int c = 0; c < C::NC; ++c) {
+    if (lane == 0) {
+      const unsigned st = pc.chunk & 1;
+      mbar_wait(&wb->chunk_empty[st], ((pc.chunk >> 1) & 1) ^ 1, a.status, a.abort_flag,
+                a.timeout_ns);
+      mbar_expect_tx(&wb->chunk_full[st], 2 * (unsigned)C::kChunkBytes);
+      unsigned char* dst = smem + L::ring_off() + st * L::kStage;
+      bulk_g2s(dst, srcA + c * C::kChunkBytes, (unsigned)C::kChunkBytes, &wb->chunk_full[st]);
+      bulk_g2s(dst + C::kChunkBytes, srcB + c * C::kChunkBytes, (unsigned)C::kChunkBytes,
+               &wb->chunk_full[st]);
+    }
+    ++pc.chunk;
+  }
+  // predecessor tile of the row panel snapshot
+  if (lane == 0) {
+    mbar_wait(&wb->p_empty, (pc.p & 1) ^ 1, a.status, a.abort_flag, a.timeout_ns);
+    mbar_expect_tx(&wb->p_full, (unsigned)C::kTile);
+    bulk_g2s(smem + L::p_off(), a.rowP + toffB, (unsigned)C::kTile, &wb->p_full);
+  }
+  ++pc.p;
+}
+
 // Optional per-task trace (sampled tasks): 10 words per entry.
 //   [0] task | type << 32   [1] SM id
 //   producer: [2] claimed  [3] inputs ready  [4] copies issued  [5] published
 //   compute : [6] descriptor seen  [9] task finished (stores issued)   [7], [8] unused
-__device__ __forceinline__ uint64_t* trace_slot(uint64_t* tr, int cap, int stride, int t) {
+__device__ __forceinline__ uint64_t* trace_slot(uint64_t* tr, int cap, int stride, int64_t t) {
   if (!tr || t < 0 || stride <= 0 || t % stride) return nullptr;
-  const int s = t / stride;
+  const int64_t s = t / stride;
   return s < cap ? tr + (size_t)s * 10 : nullptr;
 }
 __device__ __forceinline__ unsigned smid() {
@@ -277,12 +377,26 @@ __device__ __forceinline__ unsigned smid() {
   return r;
 }
 
-template <typename T, int BS>
-__global__ void __launch_bounds__(kWsThreads, 1) k_persistent_ws(Args<T> a) {
-  using L = WsLayout<BS>;
-  extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ WsBars wb;
-  __shared__ CtaScratch cs;
+// Runs f(std::integral_constant<int, BS>) for the block size of the task.
+// kFixedBS > 0: that block size only (single-graph kernels).
+template <int kFixedBS, int LBS, typename F>
+__device__ __forceinline__ auto with_bs(int bs, F&& f) {
+  if constexpr (kFixedBS > 0) {
+    return f(std::integral_constant<int, kFixedBS>{});
+  } else {
+    if (bs == 32) return f(std::integral_constant<int, 32>{});
+    if constexpr (LBS >= 64)
+      if (bs == 64) return f(std::integral_constant<int, 64>{});
+    return f(std::integral_constant<int, LBS>{});
+  }
+}
+
+// ------------------------------------------------------------------ engine ----
+
+// Src supplies: total(), next (claim counter), status / abort / timeout, trace,
+// resolve(t, &g) -> local task, args(g) -> const Args<T>&, bs(g).
+template <typename T, int kFixedBS, int LBS, class Src>
+__device__ void ws_engine(const Src& src, unsigned char* smem, WsBars& wb, CtaScratch& cs) {
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
@@ -310,14 +424,16 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_persistent_ws(Args<T> a) {
     if (lane == 0) {
       for (unsigned i = 0;; ++i) {
         const unsigned q = i % kPubDepth, ph = (i / kPubDepth) & 1;
-        if (!mbar_wait(&wb.pub_full[q], ph, a.status, a.abort_flag, a.timeout_ns)) break;
+        if (!mbar_wait(&wb.pub_full[q], ph, src.status, src.abort_flag, src.timeout_ns)) break;
         const int t = wb.pubq[q][0];
         const fwh::Task k{wb.pubq[q][1], wb.pubq[q][2], wb.pubq[q][3], wb.pubq[q][4]};
+        const int g = wb.pubq[q][5];
         if (t < 0) break;
         // tasks finish in hand-off order: the i-th completion is this task
-        if (!mbar_wait(&wb.task_done, i & 1, a.status, a.abort_flag, a.timeout_ns)) break;
-        if (t != a.skip_task) publish(a, k);
-        if (uint64_t* tr = trace_slot(a.trace, a.trace_cap, a.trace_stride, t)) tr[5] = globaltimer();
+        if (!mbar_wait(&wb.task_done, i & 1, src.status, src.abort_flag, src.timeout_ns)) break;
+        if (t != src.skip_task) publish(src.args(g), k);
+        if (uint64_t* tr = trace_slot(src.trace, src.trace_cap, src.trace_stride, t))
+          tr[5] = globaltimer();
         mbar_arrive(&wb.pub_empty[q]);
       }
     }
@@ -326,114 +442,80 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_persistent_ws(Args<T> a) {
 
   if (warp == kThreads / 32) {
     // ------------------------------------------------------------ producer
-    const int64_t total = a.stage_off[a.R + 1];
-    unsigned idesc = 0, ichunk = 0, jd = 0, jp = 0, ipub = 0;
-    auto no_idle = []() {};
+    const int64_t total = src.total();
+    unsigned idesc = 0, ipub = 0;
+    PipeCnt pc;
     for (;;) {
-      int t = -1;
+      int t = -1, g = 0;
       if (lane == 0) {
         const uint64_t tc = globaltimer();
-        const int64_t tt = atomicAdd(a.ctr, 1u);
-        int ok = tt < total && !ld_relaxed(a.abort_flag);
-        if (ok) ok = wait_deps(a, fwh::decode_task(tt, a.R, a.lookahead, a.stage_off), no_idle);
+        const int64_t tt = atomicAdd(src.next, 1u);
+        int ok = tt < total && !ld_relaxed(src.abort_flag);
+        if (ok) {
+          const fwh::Task kk = src.resolve(tt, g);
+          ok = wait_deps(src.args(g), kk);
+        }
         t = ok ? (int)tt : -1;
-        if (uint64_t* tr = trace_slot(a.trace, a.trace_cap, a.trace_stride, t)) {
+        if (uint64_t* tr = trace_slot(src.trace, src.trace_cap, src.trace_stride, t)) {
           tr[1] = smid();
           tr[2] = tc;
           tr[3] = globaltimer();
         }
       }
       t = __shfl_sync(0xffffffffu, t, 0);
+      g = __shfl_sync(0xffffffffu, g, 0);
       fwh::Task k{0, 0, 0, 0};
       bool fast = false;
+      int bs = 0;
       if (t >= 0) {
-        k = fwh::decode_task(t, a.R, a.lookahead, a.stage_off);
-        if (k.type == 3 && Num<T>::kInt && a.packed) {
-          const int slot = k.r & 1;
-          const int ba = __ldcg(a.colB + (size_t)slot * a.slot_tiles + k.ti);
-          const int bb = __ldcg(a.rowB + (size_t)slot * a.slot_tiles + k.tj);
-          fast = ba + bb < Keys<BS>::CAP;
-        }
+        int g2 = 0;
+        k = src.resolve(t, g2);
+        bs = src.bs(g);
+        fast = with_bs<kFixedBS, LBS>(bs, [&](auto B) {
+          return packed_ok<T, decltype(B)::value>(src.args(g), k);
+        });
       }
       unsigned pq = 0;
       if (lane == 0) {
         // queue the task for publication, then hand it to the compute warps
         pq = ipub % kPubDepth;
-        mbar_wait(&wb.pub_empty[pq], ((ipub / kPubDepth) & 1) ^ 1, a.status, a.abort_flag,
-                  a.timeout_ns);
+        mbar_wait(&wb.pub_empty[pq], ((ipub / kPubDepth) & 1) ^ 1, src.status, src.abort_flag,
+                  src.timeout_ns);
         wb.pubq[pq][0] = t;
         wb.pubq[pq][1] = k.type;
         wb.pubq[pq][2] = k.r;
         wb.pubq[pq][3] = k.ti;
         wb.pubq[pq][4] = k.tj;
+        wb.pubq[pq][5] = g;
         mbar_arrive(&wb.pub_full[pq]);
         const unsigned ds = idesc & 1;
-        mbar_wait(&wb.desc_empty[ds], ((idesc >> 1) & 1) ^ 1, a.status, a.abort_flag,
-                  a.timeout_ns);
+        mbar_wait(&wb.desc_empty[ds], ((idesc >> 1) & 1) ^ 1, src.status, src.abort_flag,
+                  src.timeout_ns);
         wb.desc[ds][0] = t;
         wb.desc[ds][1] = k.type;
         wb.desc[ds][2] = k.r;
         wb.desc[ds][3] = k.ti;
         wb.desc[ds][4] = k.tj;
         wb.desc[ds][5] = fast ? 1 : 0;
+        wb.desc[ds][6] = g;
         mbar_arrive(&wb.desc_full[ds]);
       }
       ++idesc;
       ++ipub;
       if (t < 0) break;
       if (k.type == 3) {
-        fence_proxy_async();  // global data published by other CTAs, read by TMA below
-        const int slot = k.r & 1;
-        // the tile's own D block, one bulk copy per valid row
-        const int64_t row0 = (int64_t)k.ti * BS, col0 = (int64_t)k.tj * BS;
-        const int nrows = (int)(a.n - row0 < (int64_t)BS ? a.n - row0 : (int64_t)BS);
-        const int ncols = (int)(a.n - col0 < (int64_t)BS ? a.n - col0 : (int64_t)BS);
-        const unsigned rowbytes = (unsigned)(((ncols + 3) / 4) * 4) * 4u;
-        if (lane == 0) {
-          mbar_wait(&wb.d_empty, (jd & 1) ^ 1, a.status, a.abort_flag, a.timeout_ns);
-          mbar_expect_tx(&wb.d_full, rowbytes * (unsigned)nrows);
-        }
-        __syncwarp();
-        unsigned char* dbuf = smem + L::d_off();
-        for (int rr = lane; rr < nrows; rr += 32)
-          bulk_g2s(dbuf + (size_t)rr * BS * sizeof(T), a.D + (row0 + rr) * a.ld + col0, rowbytes,
-                   &wb.d_full);
-        ++jd;
-        // operand chunks
-        const size_t toffA = ((size_t)slot * a.slot_tiles + k.ti) * BS * BS;
-        const size_t toffB = ((size_t)slot * a.slot_tiles + k.tj) * BS * BS;
-        const unsigned char* srcA = fast ? (const unsigned char*)(a.colK + toffA)
-                                         : (const unsigned char*)(a.colR + toffA);
-        const unsigned char* srcB = fast ? (const unsigned char*)(a.rowK + toffB)
-                                         : (const unsigned char*)(a.rowR + toffB);
-        for (int c = 0; c < L::NC; ++c) {
-          if (lane == 0) {
-            const unsigned st = ichunk & 1;
-            mbar_wait(&wb.chunk_empty[st], ((ichunk >> 1) & 1) ^ 1, a.status, a.abort_flag,
-                      a.timeout_ns);
-            mbar_expect_tx(&wb.chunk_full[st], 2 * (unsigned)L::kChunkBytes);
-            unsigned char* dst = smem + L::ring_off() + st * L::kStage;
-            bulk_g2s(dst, srcA + c * L::kChunkBytes, (unsigned)L::kChunkBytes, &wb.chunk_full[st]);
-            bulk_g2s(dst + L::kChunkBytes, srcB + c * L::kChunkBytes, (unsigned)L::kChunkBytes,
-                     &wb.chunk_full[st]);
-          }
-          ++ichunk;
-        }
-        // predecessor tile of the row panel snapshot
-        if (lane == 0) {
-          mbar_wait(&wb.p_empty, (jp & 1) ^ 1, a.status, a.abort_flag, a.timeout_ns);
-          mbar_expect_tx(&wb.p_full, (unsigned)L::kTile);
-          bulk_g2s(smem + L::p_off(), a.rowP + toffB, (unsigned)L::kTile, &wb.p_full);
-        }
-        ++jp;
+        with_bs<kFixedBS, LBS>(bs, [&](auto B) {
+          issue_operands<T, decltype(B)::value, LBS>(src.args(g), k, fast, smem, &wb, pc, lane);
+          return 0;
+        });
       } else if (lane == 0) {
         // pivot / panel tasks use the ring and Dbuf as scratch: wait until this
         // task has been published (its publication-queue slot frees up)
-        mbar_wait(&wb.pub_empty[pq], (((ipub - 1) / kPubDepth) & 1), a.status, a.abort_flag,
-                  a.timeout_ns);
+        mbar_wait(&wb.pub_empty[pq], (((ipub - 1) / kPubDepth) & 1), src.status, src.abort_flag,
+                  src.timeout_ns);
       }
       if (lane == 0) {
-        if (uint64_t* tr = trace_slot(a.trace, a.trace_cap, a.trace_stride, t)) {
+        if (uint64_t* tr = trace_slot(src.trace, src.trace_cap, src.trace_stride, t)) {
           tr[0] = (uint64_t)(unsigned)t | ((uint64_t)k.type << 32);
           tr[4] = globaltimer();
         }
@@ -444,47 +526,74 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_persistent_ws(Args<T> a) {
     // leave no bulk copy in flight: wait (bounded) for the last phase armed on
     // every full barrier
     if (lane == 0) {
-      if (jd) mbar_wait(&wb.d_full, (jd - 1) & 1, a.status, a.abort_flag, a.timeout_ns);
-      if (jp) mbar_wait(&wb.p_full, (jp - 1) & 1, a.status, a.abort_flag, a.timeout_ns);
-      for (unsigned c = ichunk >= 2 ? ichunk - 2 : 0; c < ichunk; ++c)
-        mbar_wait(&wb.chunk_full[c & 1], (c >> 1) & 1, a.status, a.abort_flag, a.timeout_ns);
+      if (pc.d) mbar_wait(&wb.d_full, (pc.d - 1) & 1, src.status, src.abort_flag, src.timeout_ns);
+      if (pc.p) mbar_wait(&wb.p_full, (pc.p - 1) & 1, src.status, src.abort_flag, src.timeout_ns);
+      for (unsigned c = pc.chunk >= 2 ? pc.chunk - 2 : 0; c < pc.chunk; ++c)
+        mbar_wait(&wb.chunk_full[c & 1], (c >> 1) & 1, src.status, src.abort_flag,
+                  src.timeout_ns);
     }
     return;
   }
 
   // -------------------------------------------------------------- compute
-  const TileCtx<T> ctx{a.D, a.P, a.n, a.ld, a.status, a.abort_flag, a.timeout_ns};
-  unsigned idesc = 0, dcnt = 0, ccnt = 0, pcnt = 0;
+  unsigned idesc = 0;
+  PipeCnt pc;
   for (;;) {
     const unsigned ds = idesc & 1;
-    if (!mbar_wait(&wb.desc_full[ds], (idesc >> 1) & 1, a.status, a.abort_flag, a.timeout_ns))
+    if (!mbar_wait(&wb.desc_full[ds], (idesc >> 1) & 1, src.status, src.abort_flag,
+                   src.timeout_ns))
       break;
     const int t = wb.desc[ds][0];
     const fwh::Task k{wb.desc[ds][1], wb.desc[ds][2], wb.desc[ds][3], wb.desc[ds][4]};
     const bool fast = wb.desc[ds][5] != 0;
+    const int g = wb.desc[ds][6];
     __syncwarp();
     if (lane == 0) mbar_arrive(&wb.desc_empty[ds]);
     ++idesc;
     if (t < 0) break;
-    uint64_t* tr = tid == 0 ? trace_slot(a.trace, a.trace_cap, a.trace_stride, t) : nullptr;
+    uint64_t* tr = tid == 0 ? trace_slot(src.trace, src.trace_cap, src.trace_stride, t) : nullptr;
     if (tr) tr[6] = globaltimer();
-    bool ok = true;
-    if (k.type == 3) {
-      ok = ws_minplus<T, BS>(ctx, k.ti, k.tj, fast, smem, &wb, dcnt, ccnt, pcnt);
-    } else if (k.type == 0) {
-      task_pivot<T, BS>(a, k.r, smem + L::ring_off(), &cs);
-      bar_compute();
-    } else {
-      // panel tasks put A in the ring region and B in Dbuf: contiguous, As + BS*BS = Dbuf
-      task_panel<T, BS>(a, k.r, k.type == 1 ? k.tj : k.ti, k.type == 1,
-                        smem + L::d_off() - (size_t)BS * BS * 4, &cs);
-      bar_compute();
-    }
+    const bool ok = with_bs<kFixedBS, LBS>(src.bs(g), [&](auto B) {
+      return compute_task<T, decltype(B)::value, LBS>(src.args(g), k, fast, smem, &wb, &cs, pc);
+    });
     if (tr) tr[9] = globaltimer();
     if (!ok) break;
     __syncwarp();
     if (lane == 0) mbar_arrive(&wb.task_done);
   }
+}
+
+// One graph: the queue of decode_task, block size BS.
+template <typename T, int BS>
+struct SingleSrc {
+  Args<T> a;
+  unsigned* next;
+  int* status;
+  int* abort_flag;
+  int64_t timeout_ns;
+  int skip_task;
+  uint64_t* trace;
+  int trace_cap, trace_stride;
+  __device__ explicit SingleSrc(const Args<T>& x)
+      : a(x), next(x.ctr), status(x.status), abort_flag(x.abort_flag), timeout_ns(x.timeout_ns),
+        skip_task(x.skip_task), trace(x.trace), trace_cap(x.trace_cap),
+        trace_stride(x.trace_stride) {}
+  __device__ int64_t total() const { return a.stage_off[a.R + 1]; }
+  __device__ fwh::Task resolve(int64_t t, int& g) const {
+    g = 0;
+    return fwh::decode_task(t, a.R, a.lookahead, a.stage_off);
+  }
+  __device__ const Args<T>& args(int) const { return a; }
+  __device__ int bs(int) const { return BS; }
+};
+
+template <typename T, int BS>
+__global__ void __launch_bounds__(kWsThreads, 1) k_persistent_ws(Args<T> a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ WsBars wb;
+  __shared__ CtaScratch cs;
+  const SingleSrc<T, BS> src(a);
+  ws_engine<T, BS, BS>(src, smem, wb, cs);
 }
 
 }  // namespace fwk

@@ -115,3 +115,29 @@ def test_queue_is_complete_and_topological(fw, R, look):
             deps += rounds_p3.get(r - 2, [])       # panel snapshot slot reuse
         for d in deps:
             assert d < idx, (q[idx].tolist(), q[d].tolist())
+
+
+def test_batched_host_checks(fw):
+    lib = fw.load()
+    import ctypes as C
+    h = C.c_void_p()
+    ns = np.array([10, 20], np.int64)
+    lds = np.array([12, 20], np.int64)
+    assert lib.fw_batched_plan_create(C.byref(h), ns.ctypes.data, lds.ctypes.data, 0, 0, None) == 1
+    bad = np.array([12, 18], np.int64)   # ld % 4 != 0
+    assert lib.fw_batched_plan_create(C.byref(h), ns.ctypes.data, bad.ctypes.data, 2, 0, None) == 1
+    small = np.array([8, 20], np.int64)  # ld < n
+    assert lib.fw_batched_plan_create(C.byref(h), ns.ctypes.data, small.ctypes.data, 2, 0, None) == 1
+    o = fw.Options.default(bs=96)
+    assert lib.fw_batched_plan_create(C.byref(h), ns.ctypes.data, lds.ctypes.data, 2, 0,
+                                      C.byref(o)) == 1
+    assert lib.fw_solve_batched(None, None, None, None) == 1
+
+
+def test_bs_table_host(fw):
+    t = fw.fw_bs_table()
+    assert len(t) == 7 and set(t.tolist()) <= {32, 64, 128}
+    with pytest.raises(fw.FWError):
+        fw.fw_bs_table(np.array([32, 32, 48, 64, 128, 128, 128], np.int32))
+    fw.fw_bs_table(t)
+    assert (fw.fw_bs_table() == t).all()

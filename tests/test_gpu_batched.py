@@ -1,0 +1,113 @@
+"""Batched solve (many graphs of uneven size in one persistent launch) against
+the CPU oracle, graph by graph, through the C ABI."""
+import numpy as np
+import pytest
+
+import graphgen
+import oracle
+from fwtest import INF, check_f32, check_int_full, fw
+
+pytestmark = pytest.mark.gpu
+
+
+def _run(Ws, options=None, reps=1):
+    import torch
+    m = fw()
+    Ds, Ps, ns, lds = [], [], [], []
+    for W in Ws:
+        n = W.shape[0]
+        ld = m.padded(n) + 4
+        tdt = torch.int32 if W.dtype == np.int32 else torch.float32
+        Db = torch.full((n, ld), -7, dtype=tdt, device="cuda")
+        Pb = torch.full((n, ld), -9, dtype=torch.int32, device="cuda")
+        Ds.append(Db)
+        Ps.append(Pb)
+        ns.append(n)
+        lds.append(ld)
+    plan = m.BatchedPlan(ns, lds, m.FW_I32 if Ws[0].dtype == np.int32 else m.FW_F32, options)
+    for _ in range(reps):
+        for W, Db in zip(Ws, Ds):
+            Db[:, :W.shape[0]].copy_(torch.from_numpy(W))
+        plan.solve([D[:, :n] for D, n in zip(Ds, ns)], [P[:, :n] for P, n in zip(Ps, ns)])
+        m.fw_sync_status()
+    bs, tasks = plan.info()
+    plan.close()
+    out = []
+    for D, P, n in zip(Ds, Ps, ns):
+        Dh, Ph = D.cpu().numpy(), P.cpu().numpy()
+        assert (Dh[:, n:] == -7).all() and (Ph[:, n:] == -9).all(), "padding written"
+        out.append((Dh[:, :n].copy(), Ph[:, :n].copy()))
+    return out, bs, tasks
+
+
+def _int_batch(seed, count, lo_n, hi_n, p=0.3, whi=100):
+    ns = graphgen.batch_sizes(seed, count, lo_n, hi_n)
+    return [graphgen.dense_graph_i32(int(n), seed=seed * 1000 + b, p=p, lo=1, hi=whi)
+            for b, n in enumerate(ns)]
+
+
+@pytest.mark.parametrize("bs", [0, 32, 64, 128])
+def test_batched_int_mixed_sizes(bs):
+    Ws = _int_batch(3, 24, 1, 300)
+    m = fw()
+    out, bsv, tasks = _run(Ws, m.Options.default(bs=bs))
+    if bs:
+        assert (bsv == bs).all()
+    for W, (D, P) in zip(Ws, out):
+        Do, Po = oracle.fw_i64(W)
+        check_int_full(W, D, P, Do, Po, oracle.path_count_i64(W, Do))
+
+
+def test_batched_replay_and_new_buffers():
+    Ws = _int_batch(5, 12, 30, 200, p=0.5)
+    out, _, _ = _run(Ws, reps=3)          # recorded once, replayed twice
+    for W, (D, P) in zip(Ws, out):
+        Do, Po = oracle.fw_i64(W)
+        check_int_full(W, D, P, Do, Po, oracle.path_count_i64(W, Do))
+
+
+def test_batched_generic_path_and_fp32():
+    Ws = _int_batch(7, 8, 20, 140, p=0.4, whi=(1 << 22))
+    out, _, _ = _run(Ws)
+    for W, (D, P) in zip(Ws, out):
+        Do, Po = oracle.fw_i64(W)
+        check_int_full(W, D, P, Do, Po, oracle.path_count_i64(W, Do))
+    ns = graphgen.batch_sizes(9, 10, 10, 260)
+    Wf = [graphgen.dense_graph_f32(int(n), seed=90 + b, p=0.5) for b, n in enumerate(ns)]
+    out, _, _ = _run(Wf)
+    for W, (D, P) in zip(Wf, out):
+        Do, Po = oracle.fw_f64(W)
+        check_f32(W, D, P, Do, Po)
+
+
+def test_batched_config_shape_sampled():
+    """The 512-graph workload (n uniform in [64, 2048], p = 0.3, weights in
+    [1, 100]): every graph checked by the GPU certificate, a sample of graphs
+    against the full oracle."""
+    import torch
+    m = fw()
+    ns = graphgen.batch_sizes(11, 512, 64, 2048)
+    Ws = [graphgen.dense_graph_i32(int(n), seed=11000 + b, p=0.3, lo=1, hi=100)
+          for b, n in enumerate(ns)]
+    out, bsv, tasks = _run(Ws)
+    assert tasks > 0
+    for b in range(len(Ws)):
+        W, (D, P) = Ws[b], out[b]
+        t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+        bad = m.fw_verify_certificate(t(W), t(D), t(P))
+        assert bad.sum() == 0, (b, bad.tolist())
+    rng = np.random.default_rng(0)
+    for b in rng.choice(len(Ws), 5, replace=False):
+        W, (D, P) = Ws[b], out[b]
+        Do, Po = oracle.fw_i64(W)
+        check_int_full(W, D, P, Do, Po, oracle.path_count_i64(W, Do))
+
+
+def test_bs_table_and_autotune():
+    m = fw()
+    old = m.fw_bs_table()
+    table, ms = m.fw_autotune_bs(m.FW_I32, graphs_per_class=6, max_n=300)
+    assert set(table.tolist()) <= {32, 64, 128}
+    assert (ms[:2] > 0).all()
+    assert (m.fw_bs_table() == table).all()
+    m.fw_bs_table(old)
