@@ -196,6 +196,30 @@ def fw_solve_host(dist: np.ndarray, pred: np.ndarray, options: Options | None = 
     check(load().fw_solve_host(dptr, pptr, n, ld, code, o, _stream_ptr(stream)), "fw_solve_host")
 
 
+def fw_backward(grad_dist, dist, pred, grad_w, stream=None) -> None:
+    """fw_backward on CUDA fp32 tensors (n x n views with a common row stride)."""
+    gp, n, ld = _matrix(grad_dist, "grad_dist")
+    dp, _, ld1 = _matrix(dist, "dist")
+    pp, _, ld2 = _matrix(pred, "pred")
+    wp, _, ld3 = _matrix(grad_w, "grad_w")
+    if len({ld, ld1, ld2, ld3}) != 1:
+        raise ValueError("all four matrices need the same row stride")
+    check(load().fw_backward(gp, dp, pp, wp, n, ld, _stream_ptr(stream)), "fw_backward")
+
+
+def fw_backward_strided(grad_dist, dist, pred, grad_w, stream=None) -> None:
+    """fw_backward_strided on (B, n, ld) CUDA tensors viewed as (B, n, n)."""
+    for t in (grad_dist, dist, pred, grad_w):
+        if t.dim() != 3 or t.stride(2) != 1 or t.stride(0) != grad_dist.stride(0) or \
+                t.stride(1) != grad_dist.stride(1):
+            raise ValueError("expected (B, n, n) views with identical strides")
+    B, n = grad_dist.shape[0], grad_dist.shape[1]
+    check(load().fw_backward_strided(grad_dist.data_ptr(), dist.data_ptr(), pred.data_ptr(),
+                                     grad_w.data_ptr(), n, grad_dist.stride(1), B,
+                                     grad_dist.stride(0), _stream_ptr(stream)),
+          "fw_backward_strided")
+
+
 def fw_sync_status(stream=None) -> None:
     check(load().fw_sync_status(_stream_ptr(stream)), "device status")
 

@@ -27,6 +27,8 @@ struct StreamWs {
   size_t hbytes = 0;
   int* status = nullptr;  // sticky status word of this stream (lives in `sbase`)
   void* sbase = nullptr;
+  void* bwd = nullptr;    // backward scratch (subtree sums)
+  size_t bwd_bytes = 0;
 };
 
 std::mutex g_mu;       // guards g_ws
@@ -178,6 +180,28 @@ fw_status solve_device(void* dist, int32_t* pred, int64_t n, int64_t ld, fw_dtyp
   return e == cudaSuccess ? FW_OK : FW_ERR_CUDA;
 }
 
+// Backward scratch of (current device, stream), grown to `bytes`.
+void* backward_scratch(cudaStream_t s, size_t bytes) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+  StreamWs& w = g_ws[{dev, s}];
+  if (w.bwd_bytes < bytes) {
+    if (w.bwd) {
+      cudaStreamSynchronize(s);
+      cudaFree(w.bwd);
+      w.bwd = nullptr;
+      w.bwd_bytes = 0;
+    }
+    if (cudaMalloc(&w.bwd, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    w.bwd_bytes = bytes;
+  }
+  return w.bwd;
+}
+
 // Status word of (current device, stream), created if the stream has none yet.
 int* status_word_for(cudaStream_t s) {
   std::lock_guard<std::mutex> lk(g_mu);
@@ -311,6 +335,7 @@ fw_status fw_release_workspace(void) {
       if (w.hd) cudaFree(w.hd);
       if (w.hp) cudaFree(w.hp);
       if (w.sbase) cudaFree(w.sbase);
+      if (w.bwd) cudaFree(w.bwd);
       it = g_ws.erase(it);
     } else {
       ++it;
