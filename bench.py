@@ -164,6 +164,125 @@ def run_reference(args):
 
 # ------------------------------------------------------------------- GPU ---
 
+def _events(k):
+    import torch
+    return [torch.cuda.Event(enable_timing=True) for _ in range(k)]
+
+
+def bench_batched(fw, args):
+    """512 digraphs, n uniform in [64, 2048], p = 0.3, int32 weights in [1, 100]:
+    one batched launch (CUDA-graph replay) vs one fw_solve launch per graph."""
+    import numpy as np
+    import torch
+    import graphgen
+    import graphgen.device as gdev
+    ns = graphgen.batch_sizes(11, 512, 64, 2048)
+    table, tune_ms = fw.fw_autotune_bs(fw.FW_I32, graphs_per_class=16, max_n=2048)
+    W, D, P = [], [], []
+    for b, n in enumerate(ns):
+        n = int(n)
+        ld = fw.padded(n)
+        w = torch.empty((n, ld), dtype=torch.int32, device="cuda")
+        gdev.fill_i32(w[:, :n], seed=11000 + b, p=0.3, lo=1, hi=100)
+        W.append(w)
+        D.append(torch.empty_like(w))
+        P.append(torch.empty_like(w))
+    plan = fw.BatchedPlan([int(n) for n in ns], [fw.padded(int(n)) for n in ns], fw.FW_I32)
+    bsv, ntasks = plan.info()
+    Dv = [d[:, :int(n)] for d, n in zip(D, ns)]
+    Pv = [p_[:, :int(n)] for p_, n in zip(P, ns)]
+
+    def restore():
+        for d, w in zip(D, W):
+            d.copy_(w)
+
+    for _ in range(2):
+        restore()
+        plan.solve(Dv, Pv)
+    fw.fw_sync_status()
+    steps = max(2, args.steps)
+    e0, e1 = _events(steps), _events(steps)
+    for i in range(steps):
+        restore()
+        e0[i].record()
+        plan.solve(Dv, Pv)
+        e1[i].record()
+    fw.fw_sync_status()
+    t_batched = sum(a.elapsed_time(b) for a, b in zip(e0, e1)) / steps
+    # one launch per graph, same buffers, same stream
+    restore()
+    for d, p_ in zip(Dv, Pv):
+        fw.fw_solve(d, p_)
+    fw.fw_sync_status()
+    restore()
+    a, b = _events(1)[0], _events(1)[0]
+    a.record()
+    for d, p_ in zip(Dv, Pv):
+        fw.fw_solve(d, p_)
+    b.record()
+    fw.fw_sync_status()
+    t_single = a.elapsed_time(b)
+    plan.close()
+    relax = float(sum(int(n) ** 3 for n in ns))
+    return {"workload": "512 digraphs, n ~ U[64,2048] (seed 11), p=0.3, int32 U[1,100]",
+            "graphs_per_s": 512 / (t_batched * 1e-3), "relax_per_s": relax / (t_batched * 1e-3),
+            "ms": t_batched, "one_launch_per_graph_ms": t_single,
+            "speedup_vs_one_launch_per_graph": t_single / t_batched,
+            "bs_table": table.tolist(), "tasks": int(ntasks),
+            "timing": "events around fw_solve_batched (graph replay); inputs restored outside"}
+
+
+def bench_backward(fw, args):
+    """64 digraphs, n = 1024, p = 0.1, fp32 weights in [1, 2): batched forward +
+    strided backward vs one forward and one backward launch per graph."""
+    import numpy as np
+    import torch
+    import graphgen.device as gdev
+    B, n = 64, 1024
+    W = torch.empty((B, n, n), dtype=torch.float32, device="cuda")
+    for b in range(B):
+        gdev.fill_f32(W[b], seed=500 + b, p=0.1, kind=1)
+    D = torch.empty_like(W)
+    P = torch.empty((B, n, n), dtype=torch.int32, device="cuda")
+    G = torch.randn((B, n, n), generator=torch.Generator(device="cuda").manual_seed(7),
+                    device="cuda")
+    GW = torch.empty_like(W)
+    plan = fw.BatchedPlan([n] * B, [n] * B, fw.FW_F32)
+    Dl = [D[b] for b in range(B)]
+    Pl = [P[b] for b in range(B)]
+    for _ in range(2):
+        D.copy_(W)
+        plan.solve(Dl, Pl)
+        fw.fw_backward_strided(G, D, P, GW)
+    fw.fw_sync_status()
+    steps = max(2, args.steps)
+    f0, f1, b1 = _events(steps), _events(steps), _events(steps)
+    for i in range(steps):
+        D.copy_(W)
+        f0[i].record()
+        plan.solve(Dl, Pl)
+        f1[i].record()
+        fw.fw_backward_strided(G, D, P, GW)
+        b1[i].record()
+    fw.fw_sync_status()
+    fwd = sum(a.elapsed_time(b) for a, b in zip(f0, f1)) / steps
+    bwd = sum(a.elapsed_time(b) for a, b in zip(f1, b1)) / steps
+    D.copy_(W)
+    a, b = _events(1)[0], _events(1)[0]
+    a.record()
+    for g in range(B):
+        fw.fw_solve(D[g], P[g])
+        fw.fw_backward(G[g], D[g], P[g], GW[g])
+    b.record()
+    fw.fw_sync_status()
+    t_single = a.elapsed_time(b)
+    plan.close()
+    return {"workload": "64 digraphs, n=1024, p=0.1, fp32 U[1,2), dL/dD ~ N(0,1)",
+            "bwd_ms": bwd, "fwd_ms": fwd, "fwd_bwd_ms": fwd + bwd,
+            "one_launch_per_graph_fwd_bwd_ms": t_single,
+            "speedup_vs_one_launch_per_graph": t_single / (fwd + bwd)}
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -290,6 +409,9 @@ def run_gpu(args):
     }
     if e2e:
         line["e2e"] = e2e
+    if not args.no_extras and world == 1:
+        line["batched"] = bench_batched(fw, args)
+        line["backward"] = bench_backward(fw, args)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)
@@ -309,6 +431,8 @@ def main():
     ap.add_argument("--driver", type=int, default=1)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched and backward measurements")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

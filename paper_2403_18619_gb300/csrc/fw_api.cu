@@ -54,7 +54,7 @@ int num_sms() {
 size_t solve_ws_bytes(int R, int BS) {
   const size_t t = (size_t)BS * BS;
   size_t b = 0;
-  b += up((size_t)R * R * 4 + 4 * 4 + 4);  // ver + ctr + abort
+  b += up(((size_t)R * R + 2 * (size_t)R) * 4 + 4 * 4 + 4);  // ver + done + ctr + abort
   b += up((size_t)(R + 2) * 4);            // stage offsets
   b += up(2 * t * 4) * 2;                  // piv, pivP
   b += up(2 * (size_t)R * t * 4) * 5;      // colK, colR, rowK, rowR, rowP
@@ -67,9 +67,10 @@ SolveWs carve_solve_ws(void* base, int R, int BS) {
   char* p = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(base) + kAlign - 1) / kAlign * kAlign);
   const size_t t = (size_t)BS * BS;
   w.ver = reinterpret_cast<int*>(p);
-  w.ctr = reinterpret_cast<unsigned*>(w.ver + (size_t)R * R);
+  w.done = w.ver + (size_t)R * R;
+  w.ctr = reinterpret_cast<unsigned*>(w.done + 2 * (size_t)R);
   w.abort_flag = reinterpret_cast<int*>(w.ctr + 4);
-  w.flags_bytes = (size_t)R * R * 4 + 4 * 4 + 4;
+  w.flags_bytes = ((size_t)R * R + 2 * (size_t)R) * 4 + 4 * 4 + 4;
   p += up(w.flags_bytes);
   w.stage_off = reinterpret_cast<unsigned*>(p);  p += up((size_t)(R + 2) * 4);
   w.piv = p;                                     p += up(2 * t * 4);

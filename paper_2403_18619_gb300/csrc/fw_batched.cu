@@ -162,7 +162,7 @@ fw_status plan_build(fw_batched_plan* p) {
   size_t flags = 0;
   for (int64_t g = 0; g < B; ++g) {
     flag_off[g] = flags;
-    flags += al((size_t)p->R[g] * p->R[g] * 4 + 4 * 4);  // ver + ctr
+    flags += al(((size_t)p->R[g] * p->R[g] + 2 * (size_t)p->R[g]) * 4 + 4 * 4);  // ver+done+ctr
   }
   flags += al(4 * 4);  // next counter + abort
   p->flags_bytes = flags;
@@ -232,7 +232,8 @@ fw_status plan_build(fw_batched_plan* p) {
     a.R = p->R[g];
     a.slot_tiles = w.slot_tiles;
     a.ver = reinterpret_cast<int*>(base + flag_off[g]);
-    a.ctr = reinterpret_cast<unsigned*>(a.ver + (size_t)p->R[g] * p->R[g]);
+    a.done = a.ver + (size_t)p->R[g] * p->R[g];
+    a.ctr = reinterpret_cast<unsigned*>(a.done + 2 * (size_t)p->R[g]);
     a.abort_flag = p->d_abort;
     a.status = nullptr;
     a.stage_off = w.stage_off;

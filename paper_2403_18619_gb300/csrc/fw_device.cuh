@@ -209,7 +209,9 @@ struct Args {
   int slot_tiles;       // tiles per snapshot slot (>= R)
   // scheduling state (persistent driver)
   int* ver;             // R*R tile versions: rounds completed on the tile
-  unsigned* ctr;        // [0] next task, [1] panel tasks done, [2] phase-4 tasks done
+  int* done;            // [2R]: panel tasks done in round r (done[r]), remaining tiles
+                        // done in round r (done[R + r]); they guard snapshot slot reuse
+  unsigned* ctr;        // [0] next task
   int* abort_flag;
   int* status;
   const unsigned* stage_off;  // R+2 queue offsets of the stages

@@ -101,6 +101,7 @@ inline void fill_stage_offsets(int R, int64_t look, unsigned* off) {
 // Device workspace of one solve (carved from one allocation).
 struct SolveWs {
   int* ver = nullptr;
+  int* done = nullptr;  // [2R]: panel tasks done per round, then remaining tiles done per round
   unsigned* ctr = nullptr;
   int* abort_flag = nullptr;
   int* status = nullptr;
@@ -115,7 +116,7 @@ struct SolveWs {
   int32_t* rowP = nullptr;
   int32_t* rowB = nullptr;
   int R = 0, BS = 0, slot_tiles = 0;
-  size_t flags_bytes = 0;  // ver + ctr + abort (zeroed before each solve)
+  size_t flags_bytes = 0;  // ver + done + ctr + abort (zeroed before each solve)
 };
 
 // Bytes needed by a solve of R tiles of BS (excluding alignment slack).

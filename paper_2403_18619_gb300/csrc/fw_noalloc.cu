@@ -67,7 +67,7 @@ cudaError_t run(T* D, int32_t* P, int64_t n, int64_t ld, unsigned char* base, in
 
   Args<T> a{};
   a.D = D; a.P = P; a.n = n; a.ld = ld; a.R = R; a.slot_tiles = ws.slot_tiles;
-  a.ver = ws.ver; a.ctr = ws.ctr; a.abort_flag = ws.abort_flag; a.status = status;
+  a.ver = ws.ver; a.done = ws.done; a.ctr = ws.ctr; a.abort_flag = ws.abort_flag; a.status = status;
   a.stage_off = ws.stage_off; a.lookahead = (int)look; a.skip_task = -1;
   a.timeout_ns = 2000000000LL; a.packed = 1;
   a.piv = reinterpret_cast<T*>(ws.piv); a.pivP = ws.pivP;

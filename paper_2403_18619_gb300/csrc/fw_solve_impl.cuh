@@ -49,7 +49,7 @@ cudaError_t launch_bs(T* D, int32_t* P, int64_t n, int64_t ld, const fwh::SolveW
                       const fwh::LaunchCfg& cfg, cudaStream_t s) {
   Args<T> a{};
   a.D = D; a.P = P; a.n = n; a.ld = ld; a.R = ws.R; a.slot_tiles = ws.slot_tiles;
-  a.ver = ws.ver; a.ctr = ws.ctr; a.abort_flag = ws.abort_flag; a.status = ws.status;
+  a.ver = ws.ver; a.done = ws.done; a.ctr = ws.ctr; a.abort_flag = ws.abort_flag; a.status = ws.status;
   a.stage_off = ws.stage_off; a.lookahead = (int)cfg.lookahead; a.skip_task = cfg.skip_task;
   a.timeout_ns = cfg.timeout_ns; a.packed = cfg.packed;
   a.piv = reinterpret_cast<T*>(ws.piv); a.pivP = ws.pivP;

@@ -223,6 +223,10 @@ __device__ bool compute_task(const Args<T>& a, const fwh::Task& k, bool fast, un
     const TileCtx<T> ctx{a.D, a.P, a.n, a.ld, a.status, a.abort_flag, a.timeout_ns};
     return ws_minplus<T, BS, LBS>(ctx, k.ti, k.tj, fast, smem, wb, pc);
   }
+  // Pivot and panel tasks overwrite the ring and Dbuf from their first
+  // instructions: every compute warp must have left the previous task (a slow
+  // warp may still be reading its last operand chunk) before any warp starts.
+  bar_compute();
   if (k.type == 0) {
     task_pivot<T, BS>(a, k.r, smem + L::ring_off(), cs);
   } else {
@@ -268,18 +272,19 @@ __device__ bool wait_deps(const Args<T>& a, const fwh::Task& k) {
   auto w = [&](const int* p, int target) {
     return wait_ge(p, target, a.abort_flag, a.status, a.timeout_ns);
   };
-  const int* done2 = reinterpret_cast<const int*>(a.ctr + 1);
-  const int* done3 = reinterpret_cast<const int*>(a.ctr + 2);
+  // Slot reuse is guarded by per-round counts: tasks of different rounds may
+  // finish out of order, so a running total could reach its target while a
+  // task of round r-2 still reads the slot.
   switch (k.type) {
-    case 0:  // pivot: its tile after round r-1; pivot slot free (panels of r-2 done)
+    case 0:  // pivot: its tile after round r-1; pivot slot free (all panels of r-2 done)
       if (!w(ver + (size_t)k.r * R + k.r, k.r)) return false;
-      if (k.r >= 2 && !w(done2, 2 * (R - 1) * (k.r - 1))) return false;
+      if (k.r >= 2 && !w(a.done + (k.r - 2), 2 * (R - 1))) return false;
       return true;
     case 1:
     case 2:  // panel: its tile after round r-1, the pivot of r, snapshot slot free
       if (!w(ver + (size_t)k.ti * R + k.tj, k.r)) return false;
       if (!w(ver + (size_t)k.r * R + k.r, k.r + 1)) return false;
-      if (k.r >= 2 && !w(done3, (R - 1) * (R - 1) * (k.r - 1))) return false;
+      if (k.r >= 2 && !w(a.done + R + (k.r - 2), (R - 1) * (R - 1))) return false;
       return true;
     default:  // remaining tile: itself after r-1, both panels of round r
       if (!w(ver + (size_t)k.ti * R + k.tj, k.r)) return false;
@@ -296,8 +301,8 @@ __device__ bool wait_deps(const Args<T>& a, const fwh::Task& k) {
 template <typename T>
 __device__ __forceinline__ void publish(const Args<T>& a, const fwh::Task& k) {
   st_release(a.ver + (size_t)k.ti * a.R + k.tj, k.r + 1);
-  if (k.type == 1 || k.type == 2) red_release_add(a.ctr + 1, 1u);
-  if (k.type == 3) red_release_add(a.ctr + 2, 1u);
+  if (k.type == 1 || k.type == 2) red_release_add(reinterpret_cast<unsigned*>(a.done + k.r), 1u);
+  if (k.type == 3) red_release_add(reinterpret_cast<unsigned*>(a.done + a.R + k.r), 1u);
 }
 
 // Whether a remaining-tile task may relax packed keys (int32, bounded panels).
