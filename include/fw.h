@@ -6,7 +6,7 @@
  * n x n distance matrix D whose entry D[i][j] is the weight of the edge i -> j
  * (INF when there is no edge, 0 on the diagonal), compute in place the length
  * of the shortest i -> j path for every pair, and a matrix P that records the
- * paths.  The blocked schedule (Sec. 2.3.1: R = ceil(n/BS) rounds of pivot
+ * paths.  The blocked schedule (Sec. 2.3, Fig. 2: R = ceil(n/BS) rounds of pivot
  * block, pivot row/column blocks, remaining blocks) and the intra-round
  * concurrency of Opt-9 (Sec. 3.2) are realised on the GPU by the kernels
  * behind these calls; the library form itself is the paper's future-work item
@@ -77,7 +77,7 @@ typedef enum {
 } fw_driver;
 
 typedef struct fw_options {
-  int32_t bs;                 /* block size BS (Sec. 2.3.1): 0 = automatic, else 32, 64 or 128 */
+  int32_t bs;                 /* block size BS (Sec. 2.3): 0 = automatic, else 32, 64 or 128 */
   int32_t driver;             /* fw_driver */
   int32_t lookahead;          /* persistent driver: remaining-block tasks of round r queued
                                  between the pivot and the panels of round r+1; -1 = automatic */
@@ -105,7 +105,7 @@ const char* fw_status_string(fw_status s);
 
 /*
  * fw_solve: all-pairs shortest paths of one graph, in place (Sec. 2.3, the
- * blocked algorithm of Sec. 2.3.1).
+ * blocked algorithm of Sec. 2.3, Fig. 2).
  *   dist  device pointer, n x ld, dtype elements; holds the weights on entry
  *         and the distances on exit.
  *   pred  device pointer, n x ld int32, output only (may not alias dist).

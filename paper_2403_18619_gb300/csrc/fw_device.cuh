@@ -1,6 +1,6 @@
 // Device-side building blocks of the blocked Floyd-Warshall solver.
 //
-// Blocked FW (Sec. 2.3.1): the matrix is cut into BS x BS tiles, R = ceil(n/BS)
+// Blocked FW (Sec. 2.3, "Blocked FW Algorithm", Fig. 2): the matrix is cut into BS x BS tiles, R = ceil(n/BS)
 // rounds; round r runs
 //   phase 1  the pivot tile (r,r): in-place FW over the BS vertices of block r,
 //   phase 2/3 the pivot row tiles (r,j) and column tiles (i,r), each relaxed
@@ -440,7 +440,7 @@ __device__ __forceinline__ void core_generic(const T* __restrict__ As, const T* 
 
 // ------------------------------------------------------------- phase 1 ----
 
-// Pivot tile (r,r): in-place FW over the vertices of block r (Sec. 2.3.1,
+// Pivot tile (r,r): in-place FW over the vertices of block r (Sec. 2.3, blocked FW,
 // phase 1).  Each step kk broadcasts row kk and column kk through shared
 // memory (double-buffered, one barrier per step) and relaxes every owned
 // element through kk with an eager strict-< predecessor update.  Writes the
@@ -524,7 +524,7 @@ __device__ __noinline__ void task_pivot(const Args<T>& a, int r, void* smem_raw,
 // Column tile: new[a][b] = min(old[a][b], min_kk old[a][kk] + Piv[kk][b]),
 //              pred from the pivot's pred row kk.
 // With the pivot already closed (phase 1), this product equals the in-place
-// sequential update of Sec. 2.3.1 phases 2 and 3.  Also writes the tile's
+// sequential update of the blocked FW phases 2 and 3 (Sec. 2.3).  Also writes the tile's
 // snapshot (packed keys, raw, pred for row tiles, and its bound) into slot r&1.
 template <typename T, int BS>
 __device__ __noinline__ void task_panel(const Args<T>& a, int r, int t, bool is_row, void* smem_raw,
@@ -696,7 +696,7 @@ __device__ __noinline__ void task_panel(const Args<T>& a, int r, int t, bool is_
 
 // Remaining tile (ti, tj) of round r: D_ij = min(D_ij, A (x) B) with A the
 // column-panel snapshot of tile row ti and B the row-panel snapshot of tile
-// column tj (Sec. 2.3.1, phase 4).  Operands arrive by two bulk copies.
+// column tj (Sec. 2.3, blocked FW, phase 4).  Operands arrive by two bulk copies.
 // `phase` is the parity of the CTA's operand mbarrier (flipped here).
 template <typename T, int BS>
 __device__ void task_minplus(const Args<T>& a, int r, int ti, int tj, void* smem_raw,

@@ -263,7 +263,7 @@ __device__ __forceinline__ bool wait_ge(const int* p, int target, int* abort_fla
   }
 }
 
-// Inputs of task k (Sec. 2.3.1 phase order, Opt-9's per-block dependencies of
+// Inputs of task k (Sec. 2.3 blocked-FW phase order, Opt-9's per-block dependencies of
 // Sec. 3.2, and the slot reuse of the double-buffered snapshots).
 template <typename T>
 __device__ bool wait_deps(const Args<T>& a, const fwh::Task& k) {
