@@ -9,8 +9,8 @@
  * paths.  The blocked schedule (Sec. 2.3, Fig. 2: R = ceil(n/BS) rounds of pivot
  * block, pivot row/column blocks, remaining blocks) and the intra-round
  * concurrency of Opt-9 (Sec. 3.2) are realised on the GPU by the kernels
- * behind these calls; the library form itself is the paper's future-work item
- * "a library for third-party C/C++ programs" (Sec. 5).
+ * behind these calls; the library form itself is the reusable library the paper
+ * lists as future work (Sec. 5).
  *
  * Conventions shared by every entry point
  *   - Matrices are row-major with leading dimension ld >= n (elements).  Rows
