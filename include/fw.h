@@ -92,9 +92,14 @@ typedef struct fw_options {
   uint64_t* trace;            /* optional device buffer of trace_cap x 10 uint64: a %globaltimer
                                  timeline of every trace_stride-th task of the persistent driver
                                  (claim, inputs ready, operands issued, published; compute start
-                                 and end), the GPU view of the idle time Opt-9 targets (Sec. 4.3) */
+                                 and end), the GPU view of the idle time Opt-9 targets (Sec. 4.3).
+                                 Min-plus tasks add SM-cycle counts: column 7 = tile-load wait |
+                                 operand-chunk waits << 32, column 8 = cycles from task start to
+                                 the end of the relaxation | whole task << 32 */
   int64_t trace_cap;
   int32_t trace_stride;
+  int32_t tile_tma;           /* persistent driver: 1 (default) loads each remaining tile with one
+                                 2-D TMA tensor copy, 0 = one bulk copy per tile row */
 } fw_options;
 
 /* Fills *opt with the defaults used by fw_solve. */

@@ -52,6 +52,7 @@ class Options(ctypes.Structure):
         ("trace", ctypes.c_void_p),
         ("trace_cap", ctypes.c_int64),
         ("trace_stride", ctypes.c_int32),
+        ("tile_tma", ctypes.c_int32),
     ]
 
     @classmethod

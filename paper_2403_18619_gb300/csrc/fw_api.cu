@@ -38,6 +38,40 @@ std::map<int, int> g_sms;
 
 }  // namespace
 
+namespace {
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = []() -> EncodeTiledFn {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return nullptr;
+    return reinterpret_cast<EncodeTiledFn>(f);
+  }();
+  return fn;
+}
+}  // namespace
+
+bool encode_tile_map(CUtensorMap* map, const void* base, int64_t n, int64_t ld, int box, bool f32) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn || n <= 0 || box <= 0 || box > 256) return false;
+  if ((reinterpret_cast<uintptr_t>(base) & 15) || ((ld * 4) & 15)) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)n};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
+  const cuuint32_t boxd[2] = {(cuuint32_t)box, (cuuint32_t)box};
+  const cuuint32_t estr[2] = {1, 1};
+  // elements outside [0, n) read as zero; the kernels mask them
+  return fn(map, f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_INT32, 2,
+            const_cast<void*>(base), dims, strides, boxd, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 int num_sms() {
   int dev = 0;
   cudaGetDevice(&dev);
@@ -134,6 +168,7 @@ fw_status check_options(const fw_options& o) {
   if (o.driver < 0 || o.driver > 2) return FW_ERR_ARG;
   if (o.grid < 0 || o.timeout_ns < 0) return FW_ERR_ARG;
   if (o.trace && (o.trace_cap <= 0 || o.trace_cap > (1 << 30) || o.trace_stride <= 0)) return FW_ERR_ARG;
+  if (o.tile_tma != 0 && o.tile_tma != 1) return FW_ERR_ARG;
   return FW_OK;
 }
 
@@ -175,6 +210,7 @@ fw_status solve_device(void* dist, int32_t* pred, int64_t n, int64_t ld, fw_dtyp
   cfg.trace = o.trace;
   cfg.trace_cap = o.trace_cap;
   cfg.trace_stride = o.trace_stride;
+  cfg.tile_tma = o.tile_tma != 0;
   cudaError_t e = dtype == FW_I32
                       ? launch_solve_i32(reinterpret_cast<int32_t*>(dist), pred, n, ld, ws, cfg, s)
                       : launch_solve_f32(reinterpret_cast<float*>(dist), pred, n, ld, ws, cfg, s);
@@ -241,6 +277,7 @@ void fw_options_default(fw_options* o) {
   o->trace = nullptr;
   o->trace_cap = 0;
   o->trace_stride = 0;
+  o->tile_tma = 1;
 }
 
 const char* fw_status_string(fw_status s) {

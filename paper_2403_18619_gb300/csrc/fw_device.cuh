@@ -35,6 +35,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 #include <type_traits>
+#include <utility>
 
 namespace fwk {
 
@@ -89,6 +90,17 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
                "r"(bytes)
                : "memory");
 }
+// 2-D tiled tensor copy global -> shared (box of the tensor map at element
+// coordinates x = column, y = row), completing on `bar`.  x * 4 bytes must be
+// a multiple of 16.
+__device__ __forceinline__ void tma_load_2d(void* dst, const void* tmap, int x, int y,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], "
+      "[%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+      "l"(tmap), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
 // 1-D bulk copy global -> shared through the TMA unit, completing on `bar`.
 // dst, src 16-byte aligned; bytes a multiple of 16.
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes,
@@ -133,6 +145,17 @@ struct Geo {
   static_assert(TM * 16 == BS && SPAN == 16 * G, "bad tile geometry");
   __device__ __forceinline__ static int idx(int t, int m) { return (m / G) * SPAN + t * G + (m % G); }
 };
+
+// Calls f(std::integral_constant<int, I>{}) for I = 0 .. N-1 (compile-time
+// loop indices, e.g. register indices of a micro-tile).
+template <class F, int... I>
+__device__ __forceinline__ void static_for_impl(F&& f, std::integer_sequence<int, I...>) {
+  (f(std::integral_constant<int, I>{}), ...);
+}
+template <int N, class F>
+__device__ __forceinline__ void static_for(F&& f) {
+  static_for_impl(f, std::make_integer_sequence<int, N>{});
+}
 
 // Packed-key parameters: KB bits hold the code kk+1 (1..BS), CAP bounds the
 // distance part so that key(A) + key(B) never wraps a uint32.
@@ -229,6 +252,9 @@ struct Args {
   T* rowR;              // raw
   int32_t* rowP;        // [2][tiles][BS*BS] predecessors of the row panel tiles
   int32_t* rowB;
+  // 2-D tensor map of D (CUtensorMap, BS x BS boxes) for the persistent
+  // driver's tile loads; null: the tile is copied row by row
+  const void* tmapD;
   // optional per-task trace (persistent driver)
   uint64_t* trace;
   int trace_cap;
@@ -240,9 +266,9 @@ struct Args {
 template <int BS>
 struct Smem {
   static constexpr int kTile = BS * BS;
-  // As and Bs are BS*BS 32-bit words each; the pivot task reuses As for its
-  // row / column broadcast buffers.
-  static constexpr size_t bytes() { return (size_t)2 * kTile * 4 + 256; }
+  // As, Bs and Ps (panel tasks' predecessor source) are BS*BS 32-bit words
+  // each; the pivot task reuses As for its row / column broadcast buffers.
+  static constexpr size_t bytes() { return (size_t)3 * kTile * 4 + 256; }
 };
 
 struct CtaScratch {
@@ -440,13 +466,248 @@ __device__ __forceinline__ void core_generic(const T* __restrict__ As, const T* 
 
 // ------------------------------------------------------------- phase 1 ----
 
-// Pivot tile (r,r): in-place FW over the vertices of block r (Sec. 2.3, blocked FW,
-// phase 1).  Each step kk broadcasts row kk and column kk through shared
-// memory (double-buffered, one barrier per step) and relaxes every owned
-// element through kk with an eager strict-< predecessor update.  Writes the
-// live tile and the pivot snapshot of slot r&1.
+// OR of a predicate over the 256 compute threads (one named barrier).
+__device__ __forceinline__ bool bar_compute_or(bool v) {
+  unsigned out;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, 256, p;\n"
+      " selp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(out)
+      : "r"(v ? 1u : 0u)
+      : "memory");
+  return out != 0;
+}
+
+// Negative-cycle check of a closed pivot tile, its stores to the live matrix
+// and to the pivot snapshot of slot r&1 (distances and predecessors apart, so
+// that the distances leave registers before predecessors are resolved).
 template <typename T, int BS>
-__device__ __noinline__ void task_pivot(const Args<T>& a, int r, void* smem_raw, CtaScratch* cs) {
+__device__ __forceinline__ void pivot_store_dist(const Args<T>& a, int r,
+                                                 const T (&d)[Geo<BS>::TM][Geo<BS>::TM], int tx,
+                                                 int ty) {
+  using Gm = Geo<BS>;
+  constexpr int TM = Gm::TM;
+  bool neg = false;
+#pragma unroll
+  for (int mm = 0; mm < TM; ++mm)
+#pragma unroll
+    for (int nn = 0; nn < TM; ++nn)
+      if (Gm::idx(ty, mm) == Gm::idx(tx, nn) && d[mm][nn] < T(0)) neg = true;
+  if (neg) atomicOr(a.status, kStNegCycle);
+  store_tile<BS>(a.D, d, a.n, a.ld, r, r, tx, ty);
+  put_tile<BS, false>(a.piv + (size_t)(r & 1) * BS * BS, d, tx, ty);
+}
+template <typename T, int BS>
+__device__ __forceinline__ void pivot_store_pred(const Args<T>& a, int r,
+                                                 const int32_t (&p)[Geo<BS>::TM][Geo<BS>::TM],
+                                                 int tx, int ty) {
+  store_tile<BS>(a.P, p, a.n, a.ld, r, r, tx, ty);
+  put_tile<BS, false>(a.pivP + (size_t)(r & 1) * BS * BS, p, tx, ty);
+}
+
+// Step kk of the packed pivot for the owners of row / column kk+1 (register
+// index MP in their micro-tiles, owner thread row / column `own`): relax those
+// elements through kk first and publish them as the broadcast of step kk+1,
+// so that the next barrier does not wait for a whole step's relaxations.
+// Re-relaxing them in the full step afterwards is a no-op (min is idempotent).
+template <int BS, int MP>
+__device__ __forceinline__ void pivot_publish_next(uint32_t (&acc)[Geo<BS>::TM][Geo<BS>::TM],
+                                                   const uint32_t (&cv)[Geo<BS>::TM],
+                                                   const uint32_t (&rv)[Geo<BS>::TM], int own,
+                                                   int kk1, uint32_t* rowK, uint32_t* colK,
+                                                   int tx, int ty) {
+  using Gm = Geo<BS>;
+  using K = Keys<BS>;
+  constexpr int TM = Gm::TM, G = Gm::G;
+  const int buf = kk1 & 1;
+  if (ty == own) {
+#pragma unroll
+    for (int nn = 0; nn < TM; ++nn) acc[MP][nn] = __viaddmin_u32(cv[MP], rv[nn], acc[MP][nn]);
+#pragma unroll
+    for (int gg = 0; gg < Gm::NG; ++gg) {
+      uint32_t v[G];
+#pragma unroll
+      for (int q = 0; q < G; ++q) v[q] = acc[MP][gg * G + q] & ~K::MASK;
+      vstore<G>(rowK + buf * BS + gg * Gm::SPAN + tx * G, v);
+    }
+  }
+  if (tx == own) {
+#pragma unroll
+    for (int mm = 0; mm < TM; ++mm) acc[mm][MP] = __viaddmin_u32(cv[mm], rv[MP], acc[mm][MP]);
+#pragma unroll
+    for (int gg = 0; gg < Gm::NG; ++gg) {
+      uint32_t v[G];
+#pragma unroll
+      for (int q = 0; q < G; ++q) v[q] = (acc[gg * G + q][MP] & ~K::MASK) + (uint32_t)(kk1 + 1);
+      vstore<G>(colK + buf * BS + gg * Gm::SPAN + ty * G, v);
+    }
+  }
+}
+
+// Packed-key pivot (int32, bounded entries).
+template <typename T, int BS>
+__device__ __noinline__ void pivot_packed(const Args<T>& a, int r, void* smem_raw) {
+  using Gm = Geo<BS>;
+  using K = Keys<BS>;
+  constexpr int TM = Gm::TM, G = Gm::G, NG = Gm::NG;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  uint32_t* rowK = reinterpret_cast<uint32_t*>(smem_raw);  // [2][BS]
+  uint32_t* colK = rowK + 2 * BS;                          // [2][BS]
+  int32_t* nxt = reinterpret_cast<int32_t*>(colK + 2 * BS);  // [BS][BS], after the steps
+  int32_t* val = nxt + BS * BS;                              // [BS][BS]
+  uint32_t acc[TM][TM];
+  {
+    T d[TM][TM];
+    int32_t p[TM][TM];
+    load_tile<BS>(d, a.D, a.n, a.ld, r, r, tx, ty, Num<T>::inf());
+    load_tile<BS>(p, a.P, a.n, a.ld, r, r, tx, ty, (int32_t)-1);
+    // the old predecessors wait in shared memory (not in registers) during the steps
+#pragma unroll
+    for (int mm = 0; mm < TM; ++mm)
+#pragma unroll
+      for (int nn = 0; nn < TM; ++nn) {
+        val[Gm::idx(ty, mm) * BS + Gm::idx(tx, nn)] = p[mm][nn];
+        acc[mm][nn] = key_of<BS>((int32_t)d[mm][nn]);
+      }
+  }
+  // broadcast of step 0: row 0 and column 0 (owner thread row / column 0, register 0)
+  if (ty == 0) {
+#pragma unroll
+    for (int gg = 0; gg < NG; ++gg) {
+      uint32_t v[G];
+#pragma unroll
+      for (int q = 0; q < G; ++q) v[q] = acc[0][gg * G + q];
+      vstore<G>(rowK + gg * Gm::SPAN + tx * G, v);
+    }
+  }
+  if (tx == 0) {
+#pragma unroll
+    for (int gg = 0; gg < NG; ++gg) {
+      uint32_t v[G];
+#pragma unroll
+      for (int q = 0; q < G; ++q) v[q] = acc[gg * G + q][0] + 1u;
+      vstore<G>(colK + gg * Gm::SPAN + ty * G, v);
+    }
+  }
+  static_for<NG>([&](auto gc) {
+    constexpr int g = decltype(gc)::value;
+#pragma unroll 1
+    for (int to = 0; to < 16; ++to) {
+      static_for<G>([&](auto ec) {
+        constexpr int e = decltype(ec)::value;
+        const int kk = g * Gm::SPAN + to * G + e;  // row kk = register g*G+e of thread row to
+        const int buf = kk & 1;
+        bar_compute();
+        uint32_t cv[TM], rv[TM];
+#pragma unroll
+        for (int gg = 0; gg < NG; ++gg) {
+          uint32_t tc[G], tr[G];
+          vload_s<G>(tc, colK + buf * BS + gg * Gm::SPAN + ty * G);
+          vload_s<G>(tr, rowK + buf * BS + gg * Gm::SPAN + tx * G);
+#pragma unroll
+          for (int q = 0; q < G; ++q) { cv[gg * G + q] = tc[q]; rv[gg * G + q] = tr[q]; }
+        }
+        // row / column kk+1 first
+        if constexpr (e + 1 < G) {
+          pivot_publish_next<BS, g * G + e + 1>(acc, cv, rv, to, kk + 1, rowK, colK, tx, ty);
+        } else {
+          if (to < 15) {
+            pivot_publish_next<BS, g * G>(acc, cv, rv, to + 1, kk + 1, rowK, colK, tx, ty);
+          } else if constexpr (g + 1 < NG) {
+            pivot_publish_next<BS, (g + 1) * G>(acc, cv, rv, 0, kk + 1, rowK, colK, tx, ty);
+          }
+        }
+#pragma unroll
+        for (int mm = 0; mm < TM; ++mm)
+#pragma unroll
+          for (int nn = 0; nn < TM; ++nn) acc[mm][nn] = __viaddmin_u32(cv[mm], rv[nn], acc[mm][nn]);
+      });
+    }
+  });
+  // distances out first; then the chains of last steps.  Element (a, b) last
+  // improved at step kk takes the final last hop of (kk, b), whose own last
+  // improving step is earlier: walk each chain down to an element that never
+  // improved and take its old predecessor.
+#pragma unroll
+  for (int mm = 0; mm < TM; ++mm)
+#pragma unroll
+    for (int nn = 0; nn < TM; ++nn)
+      nxt[Gm::idx(ty, mm) * BS + Gm::idx(tx, nn)] = (int)(acc[mm][nn] & K::MASK) - 1;
+  {
+    T d[TM][TM];
+#pragma unroll
+    for (int mm = 0; mm < TM; ++mm)
+#pragma unroll
+      for (int nn = 0; nn < TM; ++nn) {
+        const int32_t v = (int32_t)(acc[mm][nn] >> K::KB);
+        d[mm][nn] = v == K::CAP ? Num<T>::inf() : (T)v;
+      }
+    pivot_store_dist<T, BS>(a, r, d, tx, ty);
+  }
+  bar_compute();
+  constexpr int kWalk = 8;  // hops walked directly; longer chains fall back to jumping
+  int32_t p[TM][TM];
+  bool unresolved = false;
+#pragma unroll
+  for (int mm = 0; mm < TM; ++mm)
+#pragma unroll
+    for (int nn = 0; nn < TM; ++nn) {
+      const int col = Gm::idx(tx, nn);
+      int x = Gm::idx(ty, mm);
+      int k = nxt[x * BS + col];
+#pragma unroll 1
+      for (int hop = 0; hop < kWalk && k >= 0; ++hop) {
+        x = k;
+        k = nxt[k * BS + col];
+      }
+      unresolved |= k >= 0;
+      p[mm][nn] = val[x * BS + col];
+    }
+  if (bar_compute_or(unresolved)) {
+    // pointer jumping: every round doubles the resolved chain length, and a
+    // chain is at most BS long (its steps strictly decrease)
+    for (int round = 0; (1 << round) <= 2 * BS; ++round) {
+      int nk[TM][TM];
+#pragma unroll
+      for (int mm = 0; mm < TM; ++mm)
+#pragma unroll
+        for (int nn = 0; nn < TM; ++nn) {
+          const int col = Gm::idx(tx, nn);
+          const int k = nxt[Gm::idx(ty, mm) * BS + col];
+          nk[mm][nn] = -2;
+          if (k >= 0) {
+            const int nkk = nxt[k * BS + col];
+            nk[mm][nn] = nkk;
+            if (nkk < 0) p[mm][nn] = val[k * BS + col];
+          }
+        }
+      bar_compute();
+#pragma unroll
+      for (int mm = 0; mm < TM; ++mm)
+#pragma unroll
+        for (int nn = 0; nn < TM; ++nn) {
+          if (nk[mm][nn] == -2) continue;
+          const int e = Gm::idx(ty, mm) * BS + Gm::idx(tx, nn);
+          if (nk[mm][nn] < 0) {
+            val[e] = p[mm][nn];
+            nxt[e] = -1;
+          } else {
+            nxt[e] = nk[mm][nn];
+          }
+        }
+      bar_compute();
+    }
+#pragma unroll
+    for (int mm = 0; mm < TM; ++mm)
+#pragma unroll
+      for (int nn = 0; nn < TM; ++nn) p[mm][nn] = val[Gm::idx(ty, mm) * BS + Gm::idx(tx, nn)];
+  }
+  pivot_store_pred<T, BS>(a, r, p, tx, ty);
+}
+
+// Eager pivot: compare and select per relaxation (fp32, large int32 entries).
+template <typename T, int BS>
+__device__ __noinline__ void pivot_eager(const Args<T>& a, int r, void* smem_raw) {
   using Gm = Geo<BS>;
   constexpr int TM = Gm::TM, G = Gm::G;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
@@ -454,11 +715,9 @@ __device__ __noinline__ void task_pivot(const Args<T>& a, int r, void* smem_raw,
   int32_t p[TM][TM];
   load_tile<BS>(d, a.D, a.n, a.ld, r, r, tx, ty, Num<T>::inf());
   load_tile<BS>(p, a.P, a.n, a.ld, r, r, tx, ty, (int32_t)-1);
-
-  T* rowD = reinterpret_cast<T*>(smem_raw);           // [2][BS]
+  T* rowD = reinterpret_cast<T*>(smem_raw);  // [2][BS]
   int32_t* rowP = reinterpret_cast<int32_t*>(rowD + 2 * BS);
   T* colD = reinterpret_cast<T*>(rowP + 2 * BS);
-
 #pragma unroll
   for (int g = 0; g < Gm::NG; ++g) {
 #pragma unroll 1
@@ -500,35 +759,313 @@ __device__ __noinline__ void task_pivot(const Args<T>& a, int r, void* smem_raw,
       }
     }
   }
-  // negative cycle: a negative diagonal entry
-  bool neg = false;
-#pragma unroll
-  for (int mm = 0; mm < TM; ++mm)
-#pragma unroll
-    for (int nn = 0; nn < TM; ++nn)
-      if (Gm::idx(ty, mm) == Gm::idx(tx, nn) && d[mm][nn] < T(0)) neg = true;
-  if (neg) atomicOr(a.status, kStNegCycle);
+  pivot_store_dist<T, BS>(a, r, d, tx, ty);
+  pivot_store_pred<T, BS>(a, r, p, tx, ty);
+}
 
-  store_tile<BS>(a.D, d, a.n, a.ld, r, r, tx, ty);
-  store_tile<BS>(a.P, p, a.n, a.ld, r, r, tx, ty);
-  const int slot = r & 1;
-  put_tile<BS, false>(a.piv + (size_t)slot * BS * BS, d, tx, ty);
-  put_tile<BS, false>(a.pivP + (size_t)slot * BS * BS, p, tx, ty);
+// Pivot tile (r,r): in-place FW over the vertices of block r (Sec. 2.3,
+// blocked FW, phase 1).  Each step kk broadcasts row kk and column kk through
+// shared memory (double-buffered, one barrier per step) and relaxes every
+// owned element through kk.
+//
+// int32 with bounded entries: packed keys, one __viaddmin_u32 per relaxation;
+// the key's code records the LAST step that strictly improved the element.
+// That step's row entry is final from then on (a later improvement of it would
+// have improved the element again), so the element's last hop is the final
+// last hop of (kk, b): predecessors are resolved afterwards down each column.
+// Otherwise (fp32, large entries) an eager strict-< update.  Writes the live
+// tile and the pivot snapshot of slot r&1.
+template <typename T, int BS>
+__device__ __noinline__ void task_pivot(const Args<T>& a, int r, void* smem_raw, CtaScratch* cs) {
+  using Gm = Geo<BS>;
+  using K = Keys<BS>;
+  constexpr int TM = Gm::TM;
+  bool fast = false;
+  if constexpr (Num<T>::kInt) {
+    // every value formed in the closure is a path of at most BS segments of
+    // current entries; keep twice that below CAP
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    T d[TM][TM];
+    load_tile<BS>(d, a.D, a.n, a.ld, r, r, tx, ty, Num<T>::inf());
+    int bnd = 0, dummy = 0;
+#pragma unroll
+    for (int mm = 0; mm < TM; ++mm)
+#pragma unroll
+      for (int nn = 0; nn < TM; ++nn) bnd = max(bnd, bound_of<BS>(d[mm][nn]));
+    block_max2(bnd, dummy, cs);
+    fast = a.packed && (int64_t)bnd * 2 * BS < (int64_t)K::CAP;
+  }
+  if (fast)
+    pivot_packed<T, BS>(a, r, smem_raw);
+  else
+    pivot_eager<T, BS>(a, r, smem_raw);
 }
 
 // ------------------------------------------------------------- phase 2/3 ----
 
-// Panel tile of round r: a row tile (r, t) when kRow, else a column tile (t, r).
+// Micro-tile of a BS x BS buffer with row stride BS (a snapshot or smem tile).
+template <int BS, typename T>
+__device__ __forceinline__ void load_buf(T (&v)[Geo<BS>::TM][Geo<BS>::TM], const T* buf, int tx,
+                                         int ty) {
+  using Gm = Geo<BS>;
+  constexpr int G = Gm::G;
+#pragma unroll
+  for (int m = 0; m < Gm::TM; ++m)
+#pragma unroll
+    for (int g = 0; g < Gm::NG; ++g) {
+      T tmp[G];
+      vload_cg<G>(tmp, buf + Gm::idx(ty, m) * BS + g * Gm::SPAN + tx * G);
+#pragma unroll
+      for (int e = 0; e < G; ++e) v[m][g * G + e] = tmp[e];
+    }
+}
+
+// Copy a BS x BS int32 tile into shared memory (row stride BS), cooperatively
+// and coalesced: from a row-major n x ld matrix at tile (ti, tj) (entries
+// outside [0, n) read as -1), or from a contiguous BS x BS buffer when M is
+// null.
+template <int BS>
+__device__ __forceinline__ void stage_tile_i32(int32_t* dst, const int32_t* M, int64_t n, int64_t ld,
+                                               int ti, int tj, const int32_t* buf) {
+  constexpr int V = BS / 4;  // 16-byte vectors per row
+  for (int q = threadIdx.x; q < BS * V; q += kThreads) {
+    const int row = q / V, c4 = (q % V) * 4;
+    int4 v;
+    if (!M) {
+      v = __ldcg(reinterpret_cast<const int4*>(buf + row * BS + c4));
+    } else {
+      const int64_t gi = (int64_t)ti * BS + row, gj = (int64_t)tj * BS + c4;
+      v = make_int4(-1, -1, -1, -1);
+      if (gi < n && gj < n) {
+        v = __ldcg(reinterpret_cast<const int4*>(M + gi * ld + gj));
+        if (gj + 1 >= n) v.y = -1;
+        if (gj + 2 >= n) v.z = -1;
+        if (gj + 3 >= n) v.w = -1;
+      }
+    }
+    *reinterpret_cast<int4*>(dst + row * BS + c4) = v;
+  }
+}
+
+// Results of one group of G micro-tile rows (m = g*G + e) of a panel tile:
+// new values s and new predecessors np, with improved flags.  Stores them
+// (live tile, snapshot) and returns their bound.  Working one group at a time
+// keeps the epilogue's live registers at a quarter of a full micro-tile.
+template <typename T, int BS, bool is_row>
+__device__ __forceinline__ int panel_store_group(const Args<T>& a, int r, int t, int g,
+                                                 const T (&sv)[Geo<BS>::G][Geo<BS>::TM],
+                                                 const int32_t (&np)[Geo<BS>::G][Geo<BS>::TM],
+                                                 const bool (&imp)[Geo<BS>::G][Geo<BS>::TM],
+                                                 int tx, int ty) {
+  using Gm = Geo<BS>;
+  constexpr int TM = Gm::TM, G = Gm::G;
+  const int ti = is_row ? r : t, tj = is_row ? t : r;
+  const int slot = r & 1;
+  const size_t tile_off = ((size_t)slot * a.slot_tiles + t) * BS * BS;
+  int nb = 0;
+#pragma unroll
+  for (int e = 0; e < G; ++e) {
+    const int lr = Gm::idx(ty, g * G + e);
+    const int64_t gi = (int64_t)ti * BS + lr;
+#pragma unroll
+    for (int gg = 0; gg < Gm::NG; ++gg) {
+      const int lc0 = gg * Gm::SPAN + tx * G;
+      const int64_t gj0 = (int64_t)tj * BS + lc0;
+      T vs[G];
+      int32_t vp[G];
+#pragma unroll
+      for (int q = 0; q < G; ++q) {
+        vs[q] = sv[e][gg * G + q];
+        vp[q] = np[e][gg * G + q];
+        if constexpr (Num<T>::kInt) nb = max(nb, bound_of<BS>(vs[q]));
+      }
+      if (gi < a.n) {
+        if (gj0 + G <= a.n) {
+          vstore<G>(a.D + gi * a.ld + gj0, vs);
+          if constexpr (is_row) {
+            vstore<G>(a.P + gi * a.ld + gj0, vp);
+          } else {
+#pragma unroll
+            for (int q = 0; q < G; ++q)
+              if (imp[e][gg * G + q]) a.P[gi * a.ld + gj0 + q] = vp[q];
+          }
+        } else {
+#pragma unroll
+          for (int q = 0; q < G; ++q)
+            if (gj0 + q < a.n) {
+              a.D[gi * a.ld + gj0 + q] = vs[q];
+              if (is_row || imp[e][gg * G + q]) a.P[gi * a.ld + gj0 + q] = vp[q];
+            }
+        }
+      }
+      if constexpr (is_row) {
+        // B-form snapshots: raw, pred and packed key (code bits zero)
+        vstore<G>(a.rowR + tile_off + lr * BS + lc0, vs);
+        vstore<G>(a.rowP + tile_off + lr * BS + lc0, vp);
+        if constexpr (Num<T>::kInt) {
+          uint32_t kq[G];
+#pragma unroll
+          for (int q = 0; q < G; ++q) kq[q] = key_of<BS>((int32_t)vs[q]);
+          vstore<G>(a.rowK + tile_off + lr * BS + lc0, kq);
+        }
+      }
+    }
+  }
+  if constexpr (!is_row) {
+    // A-form (transposed) snapshots: raw and packed key with code = column + 1
+#pragma unroll
+    for (int nn = 0; nn < TM; ++nn) {
+      const int lc = Gm::idx(tx, nn);
+      const size_t off = tile_off + (size_t)lc * BS + g * Gm::SPAN + ty * G;
+      T vs[G];
+#pragma unroll
+      for (int e = 0; e < G; ++e) vs[e] = sv[e][nn];
+      vstore<G>(a.colR + off, vs);
+      if constexpr (Num<T>::kInt) {
+        uint32_t kq[G];
+#pragma unroll
+        for (int e = 0; e < G; ++e) kq[e] = key_of<BS>((int32_t)vs[e]) + (uint32_t)lc + 1u;
+        vstore<G>(a.colK + off, kq);
+      }
+    }
+  }
+  return nb;
+}
+
+// Relaxation and epilogue of a panel tile over packed keys (operands already
+// in shared memory as keys).  Returns the bound of the new values.
+template <typename T, int BS, bool is_row>
+__device__ __noinline__ int panel_packed(const Args<T>& a, int r, int t,
+                                         const uint32_t* As, const uint32_t* Bs, const int32_t* Ps) {
+  using Gm = Geo<BS>;
+  using K = Keys<BS>;
+  constexpr int TM = Gm::TM, G = Gm::G;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  // the tile's own old keys: B-form in Bs for a row tile, A-form in As (with
+  // the code of its column) for a column tile
+  uint32_t acc[TM][TM];
+#pragma unroll
+  for (int m = 0; m < TM; ++m)
+#pragma unroll
+    for (int gg = 0; gg < Gm::NG; ++gg) {
+      if constexpr (is_row) {
+        uint32_t v[G];
+        vload_s<G>(v, Bs + Gm::idx(ty, m) * BS + gg * Gm::SPAN + tx * G);
+#pragma unroll
+        for (int q = 0; q < G; ++q) acc[m][gg * G + q] = v[q];
+      }
+    }
+  if constexpr (!is_row) {
+#pragma unroll
+    for (int nn = 0; nn < TM; ++nn)
+#pragma unroll
+      for (int g = 0; g < Gm::NG; ++g) {
+        uint32_t v[G];
+        vload_s<G>(v, As + Gm::idx(tx, nn) * BS + g * Gm::SPAN + ty * G);
+#pragma unroll
+        for (int e = 0; e < G; ++e) acc[g * G + e][nn] = v[e] & ~K::MASK;
+      }
+  }
+  core_packed<BS>(As, Bs, acc, tx, ty);
+  // every finite value is below CAP here, so a key decodes exactly and its
+  // clamp value can only mean INF
+  int nb = 0;
+#pragma unroll
+  for (int g = 0; g < Gm::NG; ++g) {
+    T sv[G][TM];
+    int32_t np[G][TM];
+    bool imp[G][TM];
+#pragma unroll
+    for (int e = 0; e < G; ++e) {
+      const int m = g * G + e;
+#pragma unroll
+      for (int nn = 0; nn < TM; ++nn) {
+        const int lc = Gm::idx(tx, nn);
+        const int c = (int)(acc[m][nn] & K::MASK);
+        const int32_t v = (int32_t)(acc[m][nn] >> K::KB);
+        sv[e][nn] = v == K::CAP ? Num<T>::inf() : (T)v;
+        imp[e][nn] = c != 0;
+        np[e][nn] = c ? Ps[(c - 1) * BS + lc] : (is_row ? Ps[Gm::idx(ty, m) * BS + lc] : -1);
+      }
+    }
+    nb = max(nb, panel_store_group<T, BS, is_row>(a, r, t, g, sv, np, imp, tx, ty));
+  }
+  return nb;
+}
+
+// Relaxation and epilogue of a panel tile with compare and select (fp32, or
+// int32 entries beyond the packed-key bound); operands raw in shared memory.
+template <typename T, int BS, bool is_row>
+__device__ __noinline__ int panel_eager(const Args<T>& a, int r, int t, const T* As,
+                                        const T* Bs, const int32_t* Ps) {
+  using Gm = Geo<BS>;
+  constexpr int TM = Gm::TM, G = Gm::G;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  T s[TM][TM];
+  int code[TM][TM];
+  if constexpr (is_row) {
+#pragma unroll
+    for (int m = 0; m < TM; ++m)
+#pragma unroll
+      for (int gg = 0; gg < Gm::NG; ++gg) {
+        T v[G];
+        vload_s<G>(v, Bs + Gm::idx(ty, m) * BS + gg * Gm::SPAN + tx * G);
+#pragma unroll
+        for (int q = 0; q < G; ++q) s[m][gg * G + q] = v[q];
+      }
+  } else {
+#pragma unroll
+    for (int nn = 0; nn < TM; ++nn)
+#pragma unroll
+      for (int g = 0; g < Gm::NG; ++g) {
+        T v[G];
+        vload_s<G>(v, As + Gm::idx(tx, nn) * BS + g * Gm::SPAN + ty * G);
+#pragma unroll
+        for (int e = 0; e < G; ++e) s[g * G + e][nn] = v[e];
+      }
+  }
+#pragma unroll
+  for (int m = 0; m < TM; ++m)
+#pragma unroll
+    for (int nn = 0; nn < TM; ++nn) code[m][nn] = 0;
+  core_generic<BS, T>(As, Bs, s, code, tx, ty);
+  int nb = 0;
+#pragma unroll
+  for (int g = 0; g < Gm::NG; ++g) {
+    T sv[G][TM];
+    int32_t np[G][TM];
+    bool imp[G][TM];
+#pragma unroll
+    for (int e = 0; e < G; ++e) {
+      const int m = g * G + e;
+#pragma unroll
+      for (int nn = 0; nn < TM; ++nn) {
+        const int lc = Gm::idx(tx, nn);
+        const int c = code[m][nn];
+        sv[e][nn] = s[m][nn];
+        imp[e][nn] = c != 0;
+        np[e][nn] = c ? Ps[(c - 1) * BS + lc] : (is_row ? Ps[Gm::idx(ty, m) * BS + lc] : -1);
+      }
+    }
+    nb = max(nb, panel_store_group<T, BS, is_row>(a, r, t, g, sv, np, imp, tx, ty));
+  }
+  return nb;
+}
+
+// Panel tile of round r: a row tile (r, t) when is_row, else a column tile (t, r).
 // Row tile:    new[a][b] = min(old[a][b], min_kk Piv[a][kk] + old[kk][b]),
 //              pred from the tile's own old pred row kk.
 // Column tile: new[a][b] = min(old[a][b], min_kk old[a][kk] + Piv[kk][b]),
 //              pred from the pivot's pred row kk.
 // With the pivot already closed (phase 1), this product equals the in-place
-// sequential update of the blocked FW phases 2 and 3 (Sec. 2.3).  Also writes the tile's
-// snapshot (packed keys, raw, pred for row tiles, and its bound) into slot r&1.
+// sequential update of the blocked FW phases 2 and 3 (Sec. 2.3).  Also writes
+// the tile's snapshot (packed keys, raw, pred for row tiles, and its bound)
+// into slot r&1.  Shared memory: As | Bs | Ps, three BS x BS tiles; Ps holds
+// the predecessor source (own old pred for row tiles, the pivot's for column
+// tiles) so that the epilogue gathers from shared memory.
 template <typename T, int BS>
 __device__ __noinline__ void task_panel(const Args<T>& a, int r, int t, bool is_row, void* smem_raw,
-                           CtaScratch* cs) {
+                                        CtaScratch* cs) {
   using Gm = Geo<BS>;
   using K = Keys<BS>;
   constexpr int TM = Gm::TM;
@@ -538,149 +1075,74 @@ __device__ __noinline__ void task_panel(const Args<T>& a, int r, int t, bool is_
   const int slot = r & 1;
   uint32_t* As = reinterpret_cast<uint32_t*>(smem_raw);
   uint32_t* Bs = As + BS * BS;
+  int32_t* Ps = reinterpret_cast<int32_t*>(Bs + BS * BS);
 
-  T s[TM][TM], pv[TM][TM];
-  load_tile<BS>(s, a.D, a.n, a.ld, ti, tj, tx, ty, Num<T>::inf());
+  // predecessor source, staged (its loads overlap the operand loads below)
+  if (is_row)
+    stage_tile_i32<BS>(Ps, a.P, a.n, a.ld, ti, tj, nullptr);
+  else
+    stage_tile_i32<BS>(Ps, nullptr, 0, 0, 0, 0, a.pivP + (size_t)slot * BS * BS);
+
+  bool fast = false;
   {
-    const T* piv = a.piv + (size_t)slot * BS * BS;
-#pragma unroll
-    for (int m = 0; m < TM; ++m)
-#pragma unroll
-      for (int nn = 0; nn < TM; ++nn)
-        pv[m][nn] = __ldcg(piv + Gm::idx(ty, m) * BS + Gm::idx(tx, nn));
-  }
-  int bs_ = 0, bp_ = 0;
-  if constexpr (kInt) {
-#pragma unroll
-    for (int m = 0; m < TM; ++m)
-#pragma unroll
-      for (int nn = 0; nn < TM; ++nn) {
-        bs_ = max(bs_, bound_of<BS>(s[m][nn]));
-        bp_ = max(bp_, bound_of<BS>(pv[m][nn]));
-      }
-    block_max2(bs_, bp_, cs);
-  }
-  const bool fast = kInt && a.packed && (bs_ + bp_ < K::CAP);
-
-  // operands into shared memory: A-form (k-major) on the left, B-form on the right
-  if (fast) {
-    uint32_t ks[TM][TM], kp[TM][TM];
+    T s[TM][TM], pv[TM][TM];
+    load_tile<BS>(s, a.D, a.n, a.ld, ti, tj, tx, ty, Num<T>::inf());
+    load_buf<BS>(pv, a.piv + (size_t)slot * BS * BS, tx, ty);
     if constexpr (kInt) {
+      int bs_ = 0, bp_ = 0;
 #pragma unroll
       for (int m = 0; m < TM; ++m)
 #pragma unroll
         for (int nn = 0; nn < TM; ++nn) {
-          const uint32_t code = (uint32_t)Gm::idx(tx, nn) + 1u;  // column index = kk for A-form
-          ks[m][nn] = key_of<BS>((int32_t)s[m][nn]) + (is_row ? 0u : code);
-          kp[m][nn] = key_of<BS>((int32_t)pv[m][nn]) + (is_row ? code : 0u);
+          bs_ = max(bs_, bound_of<BS>(s[m][nn]));
+          bp_ = max(bp_, bound_of<BS>(pv[m][nn]));
         }
+      block_max2(bs_, bp_, cs);
+      fast = a.packed && (bs_ + bp_ < K::CAP);
     }
-    if (is_row) {
-      put_tile<BS, true>(As, kp, tx, ty);
-      put_tile<BS, false>(Bs, ks, tx, ty);
-    } else {
-      put_tile<BS, true>(As, ks, tx, ty);
-      put_tile<BS, false>(Bs, kp, tx, ty);
-    }
-  } else {
-    T* Ast = reinterpret_cast<T*>(As);
-    T* Bst = reinterpret_cast<T*>(Bs);
-    if (is_row) {
-      put_tile<BS, true>(Ast, pv, tx, ty);
-      put_tile<BS, false>(Bst, s, tx, ty);
-    } else {
-      put_tile<BS, true>(Ast, s, tx, ty);
-      put_tile<BS, false>(Bst, pv, tx, ty);
-    }
-  }
-  bar_compute();
-
-  // relax; afterwards s[][] holds the new values and code[][] the argmin + 1 (0 = unchanged)
-  int code[TM][TM];
-  if (fast) {
-    uint32_t acc[TM][TM];
+    // operands into shared memory: A-form (k-major) on the left, B-form on the right
+    if (fast) {
+      if constexpr (kInt) {
+        // keys; the A operand carries the code of its column (= kk)
 #pragma unroll
-    for (int m = 0; m < TM; ++m)
+        for (int m = 0; m < TM; ++m)
 #pragma unroll
-      for (int nn = 0; nn < TM; ++nn) acc[m][nn] = kInt ? key_of<BS>((int32_t)s[m][nn]) : 0u;
-    core_packed<BS>(As, Bs, acc, tx, ty);
-#pragma unroll
-    for (int m = 0; m < TM; ++m)
-#pragma unroll
-      for (int nn = 0; nn < TM; ++nn) {
-        code[m][nn] = (int)(acc[m][nn] & K::MASK);
-        if (code[m][nn]) s[m][nn] = (T)(int32_t)(acc[m][nn] >> K::KB);
-      }
-  } else {
-#pragma unroll
-    for (int m = 0; m < TM; ++m)
-#pragma unroll
-      for (int nn = 0; nn < TM; ++nn) code[m][nn] = 0;
-    core_generic<BS, T>(reinterpret_cast<const T*>(As), reinterpret_cast<const T*>(Bs), s, code,
-                        tx, ty);
-  }
-
-  // predecessors: gather every value first, then write (a row tile reads its own old pred)
-  int32_t np[TM][TM];
-  {
-    const int32_t* pivP = a.pivP + (size_t)slot * BS * BS;
-#pragma unroll
-    for (int m = 0; m < TM; ++m) {
-      const int64_t gi = (int64_t)ti * BS + Gm::idx(ty, m);
-#pragma unroll
-      for (int nn = 0; nn < TM; ++nn) {
-        const int64_t gj = (int64_t)tj * BS + Gm::idx(tx, nn);
-        const bool in = gi < a.n && gj < a.n;
-        int32_t old = in ? __ldcg(a.P + gi * a.ld + gj) : -1;
-        if (code[m][nn] && in) {
-          const int kk = code[m][nn] - 1;
-          if (is_row) {
-            const int64_t gk = (int64_t)r * BS + kk;   // row kk of this tile
-            old = gk < a.n ? __ldcg(a.P + gk * a.ld + gj) : -1;
-          } else {
-            old = __ldcg(pivP + kk * BS + Gm::idx(tx, nn));
+          for (int nn = 0; nn < TM; ++nn) {
+            const uint32_t code = (uint32_t)Gm::idx(tx, nn) + 1u;
+            reinterpret_cast<uint32_t(&)[TM][TM]>(pv)[m][nn] =
+                key_of<BS>((int32_t)pv[m][nn]) + (is_row ? code : 0u);
+            reinterpret_cast<uint32_t(&)[TM][TM]>(s)[m][nn] =
+                key_of<BS>((int32_t)s[m][nn]) + (is_row ? 0u : code);
           }
+        if (is_row) {
+          put_tile<BS, true>(As, reinterpret_cast<uint32_t(&)[TM][TM]>(pv), tx, ty);
+          put_tile<BS, false>(Bs, reinterpret_cast<uint32_t(&)[TM][TM]>(s), tx, ty);
+        } else {
+          put_tile<BS, true>(As, reinterpret_cast<uint32_t(&)[TM][TM]>(s), tx, ty);
+          put_tile<BS, false>(Bs, reinterpret_cast<uint32_t(&)[TM][TM]>(pv), tx, ty);
         }
-        np[m][nn] = old;
+      }
+    } else {
+      T* Ast = reinterpret_cast<T*>(As);
+      T* Bst = reinterpret_cast<T*>(Bs);
+      if (is_row) {
+        put_tile<BS, true>(Ast, pv, tx, ty);
+        put_tile<BS, false>(Bst, s, tx, ty);
+      } else {
+        put_tile<BS, true>(Ast, s, tx, ty);
+        put_tile<BS, false>(Bst, pv, tx, ty);
       }
     }
   }
   bar_compute();
-  store_tile<BS>(a.D, s, a.n, a.ld, ti, tj, tx, ty);
-  store_tile<BS>(a.P, np, a.n, a.ld, ti, tj, tx, ty);
 
-  // snapshot for phase 4 of this round
-  int nb = 0, dummy = 0;
-  if constexpr (kInt) {
-#pragma unroll
-    for (int m = 0; m < TM; ++m)
-#pragma unroll
-      for (int nn = 0; nn < TM; ++nn) nb = max(nb, bound_of<BS>(s[m][nn]));
-  }
-  const size_t tile_off = ((size_t)slot * a.slot_tiles + t) * BS * BS;
-  if (is_row) {
-    put_tile<BS, false>(a.rowR + tile_off, s, tx, ty);
-    put_tile<BS, false>(a.rowP + tile_off, np, tx, ty);
-    if constexpr (kInt) {
-      uint32_t k[TM][TM];
-#pragma unroll
-      for (int m = 0; m < TM; ++m)
-#pragma unroll
-        for (int nn = 0; nn < TM; ++nn) k[m][nn] = key_of<BS>((int32_t)s[m][nn]);
-      put_tile<BS, false>(a.rowK + tile_off, k, tx, ty);
-    }
-  } else {
-    put_tile<BS, true>(a.colR + tile_off, s, tx, ty);
-    if constexpr (kInt) {
-      uint32_t k[TM][TM];
-#pragma unroll
-      for (int m = 0; m < TM; ++m)
-#pragma unroll
-        for (int nn = 0; nn < TM; ++nn)
-          k[m][nn] = key_of<BS>((int32_t)s[m][nn]) + (uint32_t)Gm::idx(tx, nn) + 1u;
-      put_tile<BS, true>(a.colK + tile_off, k, tx, ty);
-    }
-  }
+  const T* Ast = reinterpret_cast<const T*>(As);
+  const T* Bst = reinterpret_cast<const T*>(Bs);
+  int nb = is_row ? (fast ? panel_packed<T, BS, true>(a, r, t, As, Bs, Ps)
+                          : panel_eager<T, BS, true>(a, r, t, Ast, Bst, Ps))
+                  : (fast ? panel_packed<T, BS, false>(a, r, t, As, Bs, Ps)
+                          : panel_eager<T, BS, false>(a, r, t, Ast, Bst, Ps));
+  int dummy = 0;
   if constexpr (kInt) {
     block_max2(nb, dummy, cs);
   } else {

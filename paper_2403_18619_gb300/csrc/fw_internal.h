@@ -3,6 +3,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "../../include/fw.h"
@@ -136,6 +137,7 @@ struct LaunchCfg {
   uint64_t* trace = nullptr;
   int64_t trace_cap = 0;
   int trace_stride = 0;
+  bool tile_tma = true;
 };
 
 // Enqueue one solve (init + driver).  Returns a cudaError_t.
@@ -145,5 +147,10 @@ cudaError_t launch_solve_f32(float* D, int32_t* P, int64_t n, int64_t ld, const 
                              const LaunchCfg& cfg, cudaStream_t s);
 
 int num_sms();
+
+// Tensor map of a row-major n x n matrix of 32-bit elements with leading
+// dimension ld (elements), read in box x box tiles (2-D TMA).  False when the
+// driver offers no encoder or rejects the layout; callers then copy by rows.
+bool encode_tile_map(CUtensorMap* map, const void* base, int64_t n, int64_t ld, int box, bool f32);
 
 }  // namespace fwh

@@ -101,7 +101,10 @@ cudaError_t run(T* D, int32_t* P, int64_t n, int64_t ld, unsigned char* base, in
   attr[0].val.cooperative = 1;
   lc.attrs = attr;
   lc.numAttrs = 1;
-  return cudaLaunchKernelEx(&lc, kern, a);
+  // the tensor map would be a second copy of the caller's layout per call;
+  // this entry point keeps the per-row tile copies
+  CUtensorMap tm{};
+  return cudaLaunchKernelEx(&lc, kern, a, tm, 0);
 }
 
 }  // namespace

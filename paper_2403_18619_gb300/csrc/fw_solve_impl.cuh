@@ -109,7 +109,10 @@ cudaError_t launch_bs(T* D, int32_t* P, int64_t n, int64_t ld, const fwh::SolveW
     attr[0].val.cooperative = 1;
     lc.attrs = attr;
     lc.numAttrs = 1;
-    if ((e = cudaLaunchKernelEx(&lc, kern, a)) != cudaSuccess) return e;
+    CUtensorMap tm{};
+    const int use_tmap =
+        fwh::encode_tile_map(&tm, D, n, ld, BS, !Num<T>::kInt) && cfg.tile_tma ? 1 : 0;
+    if ((e = cudaLaunchKernelEx(&lc, kern, a, tm, use_tmap)) != cudaSuccess) return e;
   }
   if (cfg.ev_stop) cudaEventRecord(cfg.ev_stop, s);
   return cudaGetLastError();

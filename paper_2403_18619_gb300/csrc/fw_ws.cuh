@@ -102,7 +102,8 @@ struct PipeCnt {
 // operand never arrived (the kernel then stops).
 template <typename T, int BS, int LBS>
 __device__ __noinline__ bool ws_minplus(TileCtx<T> c, int ti, int tj, bool fast,
-                                        unsigned char* smem, WsBars* wb, PipeCnt& pc) {
+                                        unsigned char* smem, WsBars* wb, PipeCnt& pc,
+                                        uint64_t* tr) {
   using Gm = Geo<BS>;
   using K = Keys<BS>;
   using L = WsLayout<LBS>;
@@ -117,8 +118,13 @@ __device__ __noinline__ bool ws_minplus(TileCtx<T> c, int ti, int tj, bool fast,
   const int nrow = (int)(c.n - row0 < BS ? c.n - row0 : BS);  // valid rows / columns of the tile
   const int ncol = (int)(c.n - col0 < BS ? c.n - col0 : BS);
 
+  // optional per-phase SM-cycle counts (trace): Dbuf wait, operand-chunk
+  // waits, start to end of the relaxation, whole task
+  const long long t_a = tr ? clock64() : 0;
+  long long cw = 0;
   // 1. the tile's current values (rows/columns beyond n read as INF)
   if (!mbar_wait(&wb->d_full, pc.d & 1, c.status, c.abort_flag, c.timeout_ns)) return false;
+  const long long t_b = tr ? clock64() : 0;
   T old[TM][TM];
 #pragma unroll
   for (int m = 0; m < TM; ++m) {
@@ -148,9 +154,11 @@ __device__ __noinline__ bool ws_minplus(TileCtx<T> c, int ti, int tj, bool fast,
       for (int nn = 0; nn < TM; ++nn) acc[m][nn] = kInt ? key_of<BS>((int32_t)old[m][nn]) : 0u;
     for (int ch = 0; ch < C::NC; ++ch) {
       const unsigned st = pc.chunk & 1;
+      const long long w0 = tr ? clock64() : 0;
       if (!mbar_wait(&wb->chunk_full[st], (pc.chunk >> 1) & 1, c.status, c.abort_flag,
                      c.timeout_ns))
         return false;
+      if (tr) cw += clock64() - w0;
       const uint32_t* As = reinterpret_cast<const uint32_t*>(ring + st * L::kStage);
       const uint32_t* Bs = As + kCK * BS;
       core_packed<BS, kCK>(As, Bs, acc, tx, ty);
@@ -158,19 +166,71 @@ __device__ __noinline__ bool ws_minplus(TileCtx<T> c, int ti, int tj, bool fast,
       if (lane == 0) mbar_arrive(&wb->chunk_empty[st]);
       ++pc.chunk;
     }
+    const long long t_c = tr ? clock64() : 0;
     if (!mbar_wait(&wb->p_full, pc.p & 1, c.status, c.abort_flag, c.timeout_ns)) return false;
+    if (tr) {
+      tr[7] = (uint64_t)(t_b - t_a) | ((uint64_t)cw << 32);
+      tr[8] = (uint64_t)(t_c - t_a);
+    }
+    // most tasks of later rounds improve nothing in a warp's 16 x 128 rows:
+    // one OR over the codes and a vote skip the epilogue
+    uint32_t any = 0;
 #pragma unroll
-    for (int m = 0; m < TM; ++m) {
-      const int lr = Gm::idx(ty, m);
+    for (int m = 0; m < TM; ++m)
 #pragma unroll
-      for (int nn = 0; nn < TM; ++nn) {
-        const uint32_t code = acc[m][nn] & K::MASK;
-        const int lc = Gm::idx(tx, nn);
-        if (code && lr < nrow && lc < ncol) {
-          const int32_t nv = (int32_t)(acc[m][nn] >> K::KB);
-          Drow[lr * c.ld + lc] = (T)nv;
-          Prow[lr * c.ld + lc] = Pbuf[(code - 1) * BS + lc];
-          neg |= (row0 + lr == col0 + lc) && nv < 0;
+      for (int nn = 0; nn < TM; ++nn) any |= acc[m][nn];
+    if (__any_sync(0xffffffffu, (any & K::MASK) != 0)) {
+      if (nrow == BS && ncol == BS) {
+        // D: a 16-byte vector wherever one of its G entries improved, the
+        // others rewritten unchanged.  An improved entry is a sum of operands
+        // below CAP and decodes exactly; so does an unchanged one unless its
+        // key is the clamp (old value CAP or more: INF or a large finite
+        // one), and a group holding such a key writes its improved entries
+        // one by one.  P: the improved entries only.
+        constexpr uint32_t kClampKey = (uint32_t)K::CAP << K::KB;
+#pragma unroll
+        for (int m = 0; m < TM; ++m) {
+          const int lr = Gm::idx(ty, m);
+#pragma unroll
+          for (int g = 0; g < Gm::NG; ++g) {
+            const int lc0 = g * Gm::SPAN + tx * G;
+            uint32_t cg = 0;
+            bool clamp = false;
+            T dv[G];
+#pragma unroll
+            for (int e = 0; e < G; ++e) {
+              const uint32_t kv = acc[m][g * G + e];
+              cg |= kv & K::MASK;
+              clamp |= kv == kClampKey;
+              dv[e] = (T)(int32_t)(kv >> K::KB);
+            }
+            if (cg) {
+              if (!clamp) vstore<G>(Drow + lr * c.ld + lc0, dv);
+#pragma unroll
+              for (int e = 0; e < G; ++e) {
+                const uint32_t code = acc[m][g * G + e] & K::MASK;
+                if (code) {
+                  if (clamp) Drow[lr * c.ld + lc0 + e] = dv[e];
+                  Prow[lr * c.ld + lc0 + e] = Pbuf[(code - 1) * BS + lc0 + e];
+                }
+              }
+            }
+          }
+        }
+      } else {
+#pragma unroll
+        for (int m = 0; m < TM; ++m) {
+          const int lr = Gm::idx(ty, m);
+#pragma unroll
+          for (int nn = 0; nn < TM; ++nn) {
+            const uint32_t code = acc[m][nn] & K::MASK;
+            const int lc = Gm::idx(tx, nn);
+            if (code && lr < nrow && lc < ncol) {
+              const int32_t nv = (int32_t)(acc[m][nn] >> K::KB);
+              Drow[lr * c.ld + lc] = (T)nv;
+              Prow[lr * c.ld + lc] = Pbuf[(code - 1) * BS + lc];
+            }
+          }
         }
       }
     }
@@ -182,9 +242,11 @@ __device__ __noinline__ bool ws_minplus(TileCtx<T> c, int ti, int tj, bool fast,
       for (int nn = 0; nn < TM; ++nn) arg[m][nn] = 0;
     for (int ch = 0; ch < C::NC; ++ch) {
       const unsigned st = pc.chunk & 1;
+      const long long w0 = tr ? clock64() : 0;
       if (!mbar_wait(&wb->chunk_full[st], (pc.chunk >> 1) & 1, c.status, c.abort_flag,
                      c.timeout_ns))
         return false;
+      if (tr) cw += clock64() - w0;
       const T* As = reinterpret_cast<const T*>(ring + st * L::kStage);
       const T* Bs = As + kCK * BS;
       core_generic<BS, T, kCK>(As, Bs, old, arg, tx, ty, ch * kCK);
@@ -192,7 +254,12 @@ __device__ __noinline__ bool ws_minplus(TileCtx<T> c, int ti, int tj, bool fast,
       if (lane == 0) mbar_arrive(&wb->chunk_empty[st]);
       ++pc.chunk;
     }
+    const long long t_c = tr ? clock64() : 0;
     if (!mbar_wait(&wb->p_full, pc.p & 1, c.status, c.abort_flag, c.timeout_ns)) return false;
+    if (tr) {
+      tr[7] = (uint64_t)(t_b - t_a) | ((uint64_t)cw << 32);
+      tr[8] = (uint64_t)(t_c - t_a);
+    }
 #pragma unroll
     for (int m = 0; m < TM; ++m) {
       const int lr = Gm::idx(ty, m);
@@ -207,6 +274,7 @@ __device__ __noinline__ bool ws_minplus(TileCtx<T> c, int ti, int tj, bool fast,
       }
     }
   }
+  if (tr) tr[8] |= (uint64_t)(clock64() - t_a) << 32;  // whole task
   __syncwarp();
   if (lane == 0) mbar_arrive(&wb->p_empty);
   ++pc.p;
@@ -217,11 +285,11 @@ __device__ __noinline__ bool ws_minplus(TileCtx<T> c, int ti, int tj, bool fast,
 // Any task, compute-warp side.
 template <typename T, int BS, int LBS>
 __device__ bool compute_task(const Args<T>& a, const fwh::Task& k, bool fast, unsigned char* smem,
-                             WsBars* wb, CtaScratch* cs, PipeCnt& pc) {
+                             WsBars* wb, CtaScratch* cs, PipeCnt& pc, uint64_t* tr) {
   using L = WsLayout<LBS>;
   if (k.type == 3) {
     const TileCtx<T> ctx{a.D, a.P, a.n, a.ld, a.status, a.abort_flag, a.timeout_ns};
-    return ws_minplus<T, BS, LBS>(ctx, k.ti, k.tj, fast, smem, wb, pc);
+    return ws_minplus<T, BS, LBS>(ctx, k.ti, k.tj, fast, smem, wb, pc, tr);
   }
   // Pivot and panel tasks overwrite the ring and Dbuf from their first
   // instructions: every compute warp must have left the previous task (a slow
@@ -264,34 +332,51 @@ __device__ __forceinline__ bool wait_ge(const int* p, int target, int* abort_fla
 }
 
 // Inputs of task k (Sec. 2.3 blocked-FW phase order, Opt-9's per-block dependencies of
-// Sec. 3.2, and the slot reuse of the double-buffered snapshots).
+// Sec. 3.2, and the slot reuse of the double-buffered snapshots): dependency
+// `lane` (0..2) as a counter and the value it must reach; false when the task
+// has fewer.
 template <typename T>
-__device__ bool wait_deps(const Args<T>& a, const fwh::Task& k) {
+__device__ __forceinline__ bool dep_of(const Args<T>& a, const fwh::Task& k, int lane,
+                                       const int*& p, int& target) {
   const int R = a.R;
   const int* ver = a.ver;
-  auto w = [&](const int* p, int target) {
-    return wait_ge(p, target, a.abort_flag, a.status, a.timeout_ns);
-  };
   // Slot reuse is guarded by per-round counts: tasks of different rounds may
   // finish out of order, so a running total could reach its target while a
   // task of round r-2 still reads the slot.
   switch (k.type) {
     case 0:  // pivot: its tile after round r-1; pivot slot free (all panels of r-2 done)
-      if (!w(ver + (size_t)k.r * R + k.r, k.r)) return false;
-      if (k.r >= 2 && !w(a.done + (k.r - 2), 2 * (R - 1))) return false;
-      return true;
+      if (lane == 0) { p = ver + (size_t)k.r * R + k.r; target = k.r; return true; }
+      if (lane == 1 && k.r >= 2) { p = a.done + (k.r - 2); target = 2 * (R - 1); return true; }
+      return false;
     case 1:
     case 2:  // panel: its tile after round r-1, the pivot of r, snapshot slot free
-      if (!w(ver + (size_t)k.ti * R + k.tj, k.r)) return false;
-      if (!w(ver + (size_t)k.r * R + k.r, k.r + 1)) return false;
-      if (k.r >= 2 && !w(a.done + R + (k.r - 2), (R - 1) * (R - 1))) return false;
-      return true;
+      if (lane == 0) { p = ver + (size_t)k.ti * R + k.tj; target = k.r; return true; }
+      if (lane == 1) { p = ver + (size_t)k.r * R + k.r; target = k.r + 1; return true; }
+      if (lane == 2 && k.r >= 2) {
+        p = a.done + R + (k.r - 2);
+        target = (R - 1) * (R - 1);
+        return true;
+      }
+      return false;
     default:  // remaining tile: itself after r-1, both panels of round r
-      if (!w(ver + (size_t)k.ti * R + k.tj, k.r)) return false;
-      if (!w(ver + (size_t)k.ti * R + k.r, k.r + 1)) return false;
-      if (!w(ver + (size_t)k.r * R + k.tj, k.r + 1)) return false;
-      return true;
+      if (lane == 0) { p = ver + (size_t)k.ti * R + k.tj; target = k.r; return true; }
+      if (lane == 1) { p = ver + (size_t)k.ti * R + k.r; target = k.r + 1; return true; }
+      if (lane == 2) { p = ver + (size_t)k.r * R + k.tj; target = k.r + 1; return true; }
+      return false;
   }
+}
+
+// Wait (bounded) until every input of task k exists: lane i of the producer
+// warp acquires dependency i, so the waits overlap; the warp barrier then
+// orders those acquires before the copies lane 0 issues.  Whole warp.
+template <typename T>
+__device__ bool wait_deps(const Args<T>& a, const fwh::Task& k, int lane) {
+  const int* p = nullptr;
+  int target = 0;
+  bool ok = true;
+  if (lane < 3 && dep_of(a, k, lane, p, target))
+    ok = wait_ge(p, target, a.abort_flag, a.status, a.timeout_ns);
+  return __all_sync(0xffffffffu, ok);
 }
 
 // Completion of task k: the tile's version, and the per-phase counters that
@@ -328,15 +413,26 @@ __device__ void issue_operands(const Args<T>& a, const fwh::Task& k, bool fast, 
   const int nrows = (int)(a.n - row0 < (int64_t)BS ? a.n - row0 : (int64_t)BS);
   const int ncols = (int)(a.n - col0 < (int64_t)BS ? a.n - col0 : (int64_t)BS);
   const unsigned rowbytes = (unsigned)(((ncols + 3) / 4) * 4) * 4u;
-  if (lane == 0) {
-    mbar_wait(&wb->d_empty, (pc.d & 1) ^ 1, a.status, a.abort_flag, a.timeout_ns);
-    mbar_expect_tx(&wb->d_full, rowbytes * (unsigned)nrows);
-  }
-  __syncwarp();
   unsigned char* dbuf = smem + L::d_off();
-  for (int rr = lane; rr < nrows; rr += 32)
-    bulk_g2s(dbuf + (size_t)rr * BS * sizeof(T), a.D + (row0 + rr) * a.ld + col0, rowbytes,
-             &wb->d_full);
+  if (a.tmapD) {
+    // one tensor copy of the whole box (elements beyond n arrive as zeros and
+    // are masked by the compute warps); a single instruction keeps the
+    // producer's issue slots, shared with two compute warps, free
+    if (lane == 0) {
+      mbar_wait(&wb->d_empty, (pc.d & 1) ^ 1, a.status, a.abort_flag, a.timeout_ns);
+      mbar_expect_tx(&wb->d_full, (unsigned)(BS * BS * sizeof(T)));
+      tma_load_2d(dbuf, a.tmapD, (int)col0, (int)row0, &wb->d_full);
+    }
+  } else {
+    if (lane == 0) {
+      mbar_wait(&wb->d_empty, (pc.d & 1) ^ 1, a.status, a.abort_flag, a.timeout_ns);
+      mbar_expect_tx(&wb->d_full, rowbytes * (unsigned)nrows);
+    }
+    __syncwarp();
+    for (int rr = lane; rr < nrows; rr += 32)
+      bulk_g2s(dbuf + (size_t)rr * BS * sizeof(T), a.D + (row0 + rr) * a.ld + col0, rowbytes,
+               &wb->d_full);
+  }
   ++pc.d;
   // operand chunks
   const size_t toffA = ((size_t)slot * a.slot_tiles + k.ti) * BS * BS;
@@ -370,7 +466,8 @@ __device__ void issue_operands(const Args<T>& a, const fwh::Task& k, bool fast, 
 // Optional per-task trace (sampled tasks): 10 words per entry.
 //   [0] task | type << 32   [1] SM id
 //   producer: [2] claimed  [3] inputs ready  [4] copies issued  [5] published
-//   compute : [6] descriptor seen  [9] task finished (stores issued)   [7], [8] unused
+//   compute : [6] descriptor seen  [9] task finished (stores issued)
+//   min-plus tasks: [7], [8] SM-cycle counts of the task's phases
 __device__ __forceinline__ uint64_t* trace_slot(uint64_t* tr, int cap, int stride, int64_t t) {
   if (!tr || t < 0 || stride <= 0 || t % stride) return nullptr;
   const int64_t s = t / stride;
@@ -452,29 +549,33 @@ __device__ void ws_engine(const Src& src, unsigned char* smem, WsBars& wb, CtaSc
     PipeCnt pc;
     for (;;) {
       int t = -1, g = 0;
+      uint64_t t_claim = 0;
       if (lane == 0) {
-        const uint64_t tc = globaltimer();
+        t_claim = globaltimer();
         const int64_t tt = atomicAdd(src.next, 1u);
-        int ok = tt < total && !ld_relaxed(src.abort_flag);
-        if (ok) {
-          const fwh::Task kk = src.resolve(tt, g);
-          ok = wait_deps(src.args(g), kk);
-        }
-        t = ok ? (int)tt : -1;
-        if (uint64_t* tr = trace_slot(src.trace, src.trace_cap, src.trace_stride, t)) {
-          tr[1] = smid();
-          tr[2] = tc;
-          tr[3] = globaltimer();
+        if (tt < total && !ld_relaxed(src.abort_flag)) {
+          src.resolve(tt, g);
+          t = (int)tt;
         }
       }
       t = __shfl_sync(0xffffffffu, t, 0);
       g = __shfl_sync(0xffffffffu, g, 0);
       fwh::Task k{0, 0, 0, 0};
-      bool fast = false;
-      int bs = 0;
       if (t >= 0) {
         int g2 = 0;
         k = src.resolve(t, g2);
+        if (!wait_deps(src.args(g), k, lane)) t = -1;
+      }
+      if (lane == 0) {
+        if (uint64_t* tr = trace_slot(src.trace, src.trace_cap, src.trace_stride, t)) {
+          tr[1] = smid();
+          tr[2] = t_claim;
+          tr[3] = globaltimer();
+        }
+      }
+      bool fast = false;
+      int bs = 0;
+      if (t >= 0) {
         bs = src.bs(g);
         fast = with_bs<kFixedBS, LBS>(bs, [&](auto B) {
           return packed_ok<T, decltype(B)::value>(src.args(g), k);
@@ -513,11 +614,13 @@ __device__ void ws_engine(const Src& src, unsigned char* smem, WsBars& wb, CtaSc
           issue_operands<T, decltype(B)::value, LBS>(src.args(g), k, fast, smem, &wb, pc, lane);
           return 0;
         });
-      } else if (lane == 0) {
-        // pivot / panel tasks use the ring and Dbuf as scratch: wait until this
-        // task has been published (its publication-queue slot frees up)
-        mbar_wait(&wb.pub_empty[pq], (((ipub - 1) / kPubDepth) & 1), src.status, src.abort_flag,
-                  src.timeout_ns);
+      } else {
+        if (lane == 0) {
+          // pivot / panel tasks use the ring and Dbuf as scratch: wait until
+          // this task has been published (its publication-queue slot frees up)
+          mbar_wait(&wb.pub_empty[pq], (((ipub - 1) / kPubDepth) & 1), src.status,
+                    src.abort_flag, src.timeout_ns);
+        }
       }
       if (lane == 0) {
         if (uint64_t* tr = trace_slot(src.trace, src.trace_cap, src.trace_stride, t)) {
@@ -559,7 +662,7 @@ __device__ void ws_engine(const Src& src, unsigned char* smem, WsBars& wb, CtaSc
     uint64_t* tr = tid == 0 ? trace_slot(src.trace, src.trace_cap, src.trace_stride, t) : nullptr;
     if (tr) tr[6] = globaltimer();
     const bool ok = with_bs<kFixedBS, LBS>(src.bs(g), [&](auto B) {
-      return compute_task<T, decltype(B)::value, LBS>(src.args(g), k, fast, smem, &wb, &cs, pc);
+      return compute_task<T, decltype(B)::value, LBS>(src.args(g), k, fast, smem, &wb, &cs, pc, tr);
     });
     if (tr) tr[9] = globaltimer();
     if (!ok) break;
@@ -579,10 +682,12 @@ struct SingleSrc {
   int skip_task;
   uint64_t* trace;
   int trace_cap, trace_stride;
-  __device__ explicit SingleSrc(const Args<T>& x)
+  __device__ SingleSrc(const Args<T>& x, const void* tmapD)
       : a(x), next(x.ctr), status(x.status), abort_flag(x.abort_flag), timeout_ns(x.timeout_ns),
         skip_task(x.skip_task), trace(x.trace), trace_cap(x.trace_cap),
-        trace_stride(x.trace_stride) {}
+        trace_stride(x.trace_stride) {
+    a.tmapD = tmapD;
+  }
   __device__ int64_t total() const { return a.stage_off[a.R + 1]; }
   __device__ fwh::Task resolve(int64_t t, int& g) const {
     g = 0;
@@ -593,11 +698,12 @@ struct SingleSrc {
 };
 
 template <typename T, int BS>
-__global__ void __launch_bounds__(kWsThreads, 1) k_persistent_ws(Args<T> a) {
+__global__ void __launch_bounds__(kWsThreads, 1)
+    k_persistent_ws(Args<T> a, const __grid_constant__ CUtensorMap tmD, int use_tmap) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ WsBars wb;
   __shared__ CtaScratch cs;
-  const SingleSrc<T, BS> src(a);
+  const SingleSrc<T, BS> src(a, use_tmap ? &tmD : nullptr);
   ws_engine<T, BS, BS>(src, smem, wb, cs);
 }
 

@@ -19,7 +19,7 @@ def fw():
 
 
 def gpu_solve(W: np.ndarray, *, bs=0, driver=0, packed=1, extra_ld=0, lookahead=-1, grid=0,
-              stream=None, check_canary=True):
+              stream=None, check_canary=True, tile_tma=1):
     """Solve a host matrix on the GPU through the C ABI; returns host (D, P)."""
     import torch
     m = fw()
@@ -33,7 +33,7 @@ def gpu_solve(W: np.ndarray, *, bs=0, driver=0, packed=1, extra_ld=0, lookahead=
     D, P = Dbuf[:, :n], Pbuf[:, :n]
     D.copy_(torch.from_numpy(np.ascontiguousarray(W)))
     opt = m.Options.default(bs=bs, driver=driver, packed_keys=packed, lookahead=lookahead,
-                            grid=grid)
+                            grid=grid, tile_tma=tile_tma)
     m.fw_solve_ex(D, P, opt, stream)
     m.fw_sync_status(stream)
     Dh, Ph = Dbuf.cpu().numpy(), Pbuf.cpu().numpy()

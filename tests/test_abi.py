@@ -47,6 +47,7 @@ def test_status_strings_and_defaults(fw):
         assert lib.fw_status_string(code)
     o = fw.Options.default()
     assert o.bs == 0 and o.packed_keys == 1 and o.debug_skip_release == -1 and o.lookahead == -1
+    assert o.tile_tma == 1
 
 
 def test_host_argument_checks(fw):
@@ -63,6 +64,8 @@ def test_host_argument_checks(fw):
     bad = fw.Options.default(bs=48)
     assert lib.fw_solve_ex(good, good + 4096, 8, 8, I32, ctypes.byref(bad), None) == 1
     bad = fw.Options.default(driver=9)
+    assert lib.fw_solve_ex(good, good + 4096, 8, 8, I32, ctypes.byref(bad), None) == 1
+    bad = fw.Options.default(tile_tma=2)
     assert lib.fw_solve_ex(good, good + 4096, 8, 8, I32, ctypes.byref(bad), None) == 1
     assert lib.fw_solve_host(None, None, 8, 8, I32, None, None) == 1
     assert lib.fw_queue_tasks(0, 0, 0, 0, None) == 1

@@ -28,6 +28,22 @@ def test_int_sizes(n, bs, driver):
     check_int_full(W, D, P, Do, Po, cnt)
 
 
+@pytest.mark.parametrize("tile_tma", [0, 1])
+@pytest.mark.parametrize("n,bs,extra_ld", [(33, 32, 0), (130, 64, 12), (257, 128, 4),
+                                           (600, 128, 0)])
+def test_tile_load_paths(n, bs, extra_ld, tile_tma):
+    """The persistent driver's two ways of loading a remaining tile: one 2-D
+    tensor copy (ragged edges zero-filled by the copy, masked by the kernel;
+    padding columns never read) and one bulk copy per row."""
+    W, Do, Po, cnt = int_case(n, 77 + n, 0.4, 1, 60)
+    D, P = gpu_solve(W, bs=bs, driver=PERSISTENT, extra_ld=extra_ld, tile_tma=tile_tma)
+    check_int_full(W, D, P, Do, Po, cnt)
+    Wf = graphgen.dense_graph_f32(n, seed=n + 5, p=0.4)
+    Dfo, Pfo = oracle.fw_f64(Wf)
+    Df, Pf = gpu_solve(Wf, bs=bs, driver=PERSISTENT, extra_ld=extra_ld, tile_tma=tile_tma)
+    check_f32(Wf, Df, Pf, Dfo, Pfo)
+
+
 @pytest.mark.parametrize("driver", [PERSISTENT, PHASED])
 def test_int_config_small(driver):
     """n=1024 complete digraph, weights uniform in [1,100], BS=32."""
