@@ -94,8 +94,9 @@ typedef struct fw_options {
                                  (claim, inputs ready, operands issued, published; compute start
                                  and end), the GPU view of the idle time Opt-9 targets (Sec. 4.3).
                                  Min-plus tasks add SM-cycle counts: column 7 = tile-load wait |
-                                 operand-chunk waits << 32, column 8 = cycles from task start to
-                                 the end of the relaxation | whole task << 32 */
+                                 operand-chunk waits << 20 | predecessor-tile wait << 40 (20 bits
+                                 each, saturating), column 8 = cycles from task start to the end
+                                 of the relaxation | whole task << 32 */
   int64_t trace_cap;
   int32_t trace_stride;
   int32_t tile_tma;           /* persistent driver: 1 (default) loads each remaining tile with one

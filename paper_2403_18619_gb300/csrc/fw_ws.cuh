@@ -80,6 +80,11 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, int* s
   return false;
 }
 
+// A cycle count clamped to 20 bits (three of them share a trace word).
+__device__ __forceinline__ uint64_t cyc20(long long c) {
+  return (uint64_t)(c < 0 ? 0 : c > 0xfffff ? 0xfffff : c);
+}
+
 // Scalars the compute warps need, passed by value (kept in registers).
 template <typename T>
 struct TileCtx {
@@ -119,7 +124,7 @@ __device__ __noinline__ bool ws_minplus(TileCtx<T> c, int ti, int tj, bool fast,
   const int ncol = (int)(c.n - col0 < BS ? c.n - col0 : BS);
 
   // optional per-phase SM-cycle counts (trace): Dbuf wait, operand-chunk
-  // waits, start to end of the relaxation, whole task
+  // waits, predecessor-tile wait; start to end of the relaxation, whole task
   const long long t_a = tr ? clock64() : 0;
   long long cw = 0;
   // 1. the tile's current values (rows/columns beyond n read as INF)
@@ -169,7 +174,7 @@ __device__ __noinline__ bool ws_minplus(TileCtx<T> c, int ti, int tj, bool fast,
     const long long t_c = tr ? clock64() : 0;
     if (!mbar_wait(&wb->p_full, pc.p & 1, c.status, c.abort_flag, c.timeout_ns)) return false;
     if (tr) {
-      tr[7] = (uint64_t)(t_b - t_a) | ((uint64_t)cw << 32);
+      tr[7] = cyc20(t_b - t_a) | (cyc20(cw) << 20) | (cyc20(clock64() - t_c) << 40);
       tr[8] = (uint64_t)(t_c - t_a);
     }
     // most tasks of later rounds improve nothing in a warp's 16 x 128 rows:
@@ -257,7 +262,7 @@ __device__ __noinline__ bool ws_minplus(TileCtx<T> c, int ti, int tj, bool fast,
     const long long t_c = tr ? clock64() : 0;
     if (!mbar_wait(&wb->p_full, pc.p & 1, c.status, c.abort_flag, c.timeout_ns)) return false;
     if (tr) {
-      tr[7] = (uint64_t)(t_b - t_a) | ((uint64_t)cw << 32);
+      tr[7] = cyc20(t_b - t_a) | (cyc20(cw) << 20) | (cyc20(clock64() - t_c) << 40);
       tr[8] = (uint64_t)(t_c - t_a);
     }
 #pragma unroll
