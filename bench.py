@@ -399,12 +399,12 @@ def run_gpu(args):
                    "l2": "no flush: 8 GiB of dist+pred per step, far above the 129 MB L2"},
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": rps / 1e12,
                      "unit": "Trelax/s", "frac": achieved / rps, "traffic": None,
-                     "kernel": "k_persistent<int,128>",
+                     "kernel": "k_persistent_ws<int,128>",
                      "peak_source": "fw_peak_probe (__viaddmin_u32 chains on all SMs, same "
                                     "process, %.1f relax/SM-clk at %.0f MHz)" % (per_clk,
                                                                                   probe_mhz)},
         "clocks": clocks.summary(),
-        "gpu_launches": 2 * args.steps,
+        "gpu_launches": 3 * args.steps,  # init, persistent solver, predecessor resolution
         "wall_s_timed_region": wall,
     }
     if e2e:

@@ -30,7 +30,9 @@
  *     ">="; this library relaxes only on a strict improvement and stores the
  *     last hop, which makes pred independent of the blocked visiting order on
  *     every pair whose shortest path is unique.  Where several shortest paths
- *     exist, pred is the last hop of one of them.
+ *     exist, pred is the last hop of one of them.  While an int32 solve runs,
+ *     pred also holds intermediate entries (values <= -2); the final values
+ *     are in place once the stream has passed the call's last kernel.
  *   - Device calls are asynchronous and stream-ordered on `stream` (a
  *     cudaStream_t; NULL is the legacy default stream).  Argument errors are
  *     detected on the host and returned before anything is launched.  Errors
@@ -88,7 +90,8 @@ typedef struct fw_options {
   int32_t debug_skip_release; /* >= 0: the persistent driver never publishes the completion of
                                  this task index, so that its dependents time out; -1 = off */
   void* ev_start;             /* optional cudaEvent_t recorded just before the solver kernels */
-  void* ev_stop;              /* optional cudaEvent_t recorded just after them */
+  void* ev_stop;              /* optional cudaEvent_t recorded just after them (before the
+                                 int32 solve's final predecessor-resolution pass) */
   uint64_t* trace;            /* optional device buffer of trace_cap x 10 uint64: a %globaltimer
                                  timeline of every trace_stride-th task of the persistent driver
                                  (claim, inputs ready, operands issued, published; compute start

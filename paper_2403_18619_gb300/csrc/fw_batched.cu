@@ -84,6 +84,19 @@ __global__ void __launch_bounds__(256) k_batched_init(const Args<T>* graphs) {
   }
 }
 
+// int32: every graph's via-coded predecessor entries become last hops (see
+// ViaPred in fw_device.cuh); blockIdx.y is the graph.
+__global__ void __launch_bounds__(256) k_batched_resolve(const Args<int32_t>* graphs) {
+  const Args<int32_t> a = graphs[blockIdx.y];
+  const int64_t total = a.n * a.n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / a.n, j = e - i * a.n;
+    const int32_t pv = a.P[i * a.ld + j];
+    if (pv <= -2) a.P[i * a.ld + j] = resolve_pred(pv, a.P, a.ld, j);
+  }
+}
+
 }  // namespace fwk
 
 namespace fwh {
@@ -311,7 +324,16 @@ cudaError_t enqueue(fw_batched_plan* p, cudaStream_t s) {
   attr[0].val.cooperative = 1;
   lc.attrs = attr;
   lc.numAttrs = 1;
-  return cudaLaunchKernelEx(&lc, fwk::k_batched_ws<T>, bp);
+  if ((e = cudaLaunchKernelEx(&lc, fwk::k_batched_ws<T>, bp)) != cudaSuccess) return e;
+  if constexpr (fwk::ViaPred<T>::kOn) {
+    for (int64_t g0 = 0; g0 < p->batch; g0 += 65535) {
+      const unsigned gy = (unsigned)std::min<int64_t>(p->batch - g0, 65535);
+      fwk::k_batched_resolve<<<dim3(gx, gy), 256, 0, s>>>(
+          reinterpret_cast<const fwk::Args<int32_t>*>(args + g0));
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+  }
+  return cudaSuccess;
 }
 
 template <typename T>

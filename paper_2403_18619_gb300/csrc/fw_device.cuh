@@ -385,6 +385,28 @@ __device__ __forceinline__ int bound_of(T v) {
   }
 }
 
+// Predecessors of the int32 solver ("via" encoding).  A remaining-tile task
+// that improves (i, j) through vertex k = r*BS + kk records -(k + 2) instead of
+// gathering the last hop of (k, j).  (k, j) cannot improve again while (i, j)
+// still records k: a later strict improvement of (k, j) through block r'
+// improves (i, j) through block r' as well (integer sums are exact).  So the
+// last hop of (i, j) is that of (k, j), which may itself be a via code of an
+// earlier round; pivot and panel tasks copy such entries as they are, and
+// k_resolve_pred follows each chain (at most R links, each to an earlier
+// round) once the solve is done.  fp32 keeps gathering real last hops: float
+// sums are not associative, and the argument needs them to be.
+template <typename T>
+struct ViaPred {
+  static constexpr bool kOn = Num<T>::kInt;
+};
+__device__ __forceinline__ int32_t via_code(int64_t k) { return (int32_t)(-(k + 2)); }
+// The last hop that entry p of column j stands for (p itself unless a via code).
+__device__ __forceinline__ int32_t resolve_pred(int32_t p, const int32_t* P, int64_t ld,
+                                                int64_t j) {
+  for (int hop = 0; p <= -2 && hop <= 1024; ++hop) p = P[(int64_t)(-(int64_t)p - 2) * ld + j];
+  return p;
+}
+
 // CTA-wide maximum of two ints (every thread gets the result).
 __device__ __forceinline__ void block_max2(int& a, int& b, CtaScratch* cs) {
 #pragma unroll
@@ -901,7 +923,7 @@ __device__ __forceinline__ int panel_store_group(const Args<T>& a, int r, int t,
       if constexpr (is_row) {
         // B-form snapshots: raw, pred and packed key (code bits zero)
         vstore<G>(a.rowR + tile_off + lr * BS + lc0, vs);
-        vstore<G>(a.rowP + tile_off + lr * BS + lc0, vp);
+        if constexpr (!ViaPred<T>::kOn) vstore<G>(a.rowP + tile_off + lr * BS + lc0, vp);
         if constexpr (Num<T>::kInt) {
           uint32_t kq[G];
 #pragma unroll
@@ -1225,7 +1247,9 @@ __device__ void task_minplus(const Args<T>& a, int r, int ti, int tj, void* smem
         if (c && gi < a.n && gj < a.n) {
           const int32_t nv = (int32_t)(acc[m][nn] >> K::KB);
           a.D[gi * a.ld + gj] = (T)nv;
-          a.P[gi * a.ld + gj] = __ldcg(rowP + (c - 1) * BS + Gm::idx(tx, nn));
+          a.P[gi * a.ld + gj] = ViaPred<T>::kOn
+                                    ? via_code((int64_t)r * BS + c - 1)
+                                    : __ldcg(rowP + (c - 1) * BS + Gm::idx(tx, nn));
           if (gi == gj && nv < 0) neg = true;
         }
       }
@@ -1246,7 +1270,9 @@ __device__ void task_minplus(const Args<T>& a, int r, int ti, int tj, void* smem
         const int64_t gj = (int64_t)tj * BS + Gm::idx(tx, nn);
         if (arg[m][nn] && gi < a.n && gj < a.n) {
           a.D[gi * a.ld + gj] = old[m][nn];
-          a.P[gi * a.ld + gj] = __ldcg(rowP + (arg[m][nn] - 1) * BS + Gm::idx(tx, nn));
+          a.P[gi * a.ld + gj] = ViaPred<T>::kOn
+                                    ? via_code((int64_t)r * BS + arg[m][nn] - 1)
+                                    : __ldcg(rowP + (arg[m][nn] - 1) * BS + Gm::idx(tx, nn));
           if (gi == gj && old[m][nn] < T(0)) neg = true;
         }
       }
@@ -1267,6 +1293,20 @@ __global__ void __launch_bounds__(256) k_init_pred(const T* __restrict__ D, int3
     const int64_t i = e / n, j = e - i * n;
     const T w = D[i * ld + j];
     P[i * ld + j] = (i != j && Num<T>::finite(w)) ? (int32_t)i : -1;
+  }
+}
+
+// Final pass of an int32 solve: every via code becomes the last hop its chain
+// ends in (see ViaPred).  In place: a concurrent reader of an entry sees
+// either its via code or the last hop that code resolves to, and follows
+// either to the same end.
+static __global__ void __launch_bounds__(256) k_resolve_pred(int32_t* P, int64_t n, int64_t ld) {
+  const int64_t total = n * n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / n, j = e - i * n;
+    const int32_t p = P[i * ld + j];
+    if (p <= -2) P[i * ld + j] = resolve_pred(p, P, ld, j);
   }
 }
 

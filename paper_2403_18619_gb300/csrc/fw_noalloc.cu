@@ -104,7 +104,12 @@ cudaError_t run(T* D, int32_t* P, int64_t n, int64_t ld, unsigned char* base, in
   // the tensor map would be a second copy of the caller's layout per call;
   // this entry point keeps the per-row tile copies
   CUtensorMap tm{};
-  return cudaLaunchKernelEx(&lc, kern, a, tm, 0);
+  if ((e = cudaLaunchKernelEx(&lc, kern, a, tm, 0)) != cudaSuccess) return e;
+  if constexpr (ViaPred<T>::kOn) {
+    k_resolve_pred<<<(int)blocks, 256, 0, s>>>(P, n, ld);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 }  // namespace

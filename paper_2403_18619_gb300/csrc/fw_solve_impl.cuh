@@ -115,6 +115,13 @@ cudaError_t launch_bs(T* D, int32_t* P, int64_t n, int64_t ld, const fwh::SolveW
     if ((e = cudaLaunchKernelEx(&lc, kern, a, tm, use_tmap)) != cudaSuccess) return e;
   }
   if (cfg.ev_stop) cudaEventRecord(cfg.ev_stop, s);
+  if constexpr (ViaPred<T>::kOn) {
+    int64_t blocks = (n * n + 255) / 256;
+    const int cap = fwh::num_sms() * 8;
+    if (blocks > cap) blocks = cap;
+    k_resolve_pred<<<(int)blocks, 256, 0, s>>>(P, n, ld);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
   return cudaGetLastError();
 }
 

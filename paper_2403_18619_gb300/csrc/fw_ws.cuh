@@ -91,6 +91,7 @@ struct TileCtx {
   T* D;
   int32_t* P;
   int64_t n, ld;
+  int r;                // round
   int* status;
   int* abort_flag;
   int64_t timeout_ns;
@@ -122,6 +123,7 @@ __device__ __noinline__ bool ws_minplus(TileCtx<T> c, int ti, int tj, bool fast,
   const int64_t row0 = (int64_t)ti * BS, col0 = (int64_t)tj * BS;
   const int nrow = (int)(c.n - row0 < BS ? c.n - row0 : BS);  // valid rows / columns of the tile
   const int ncol = (int)(c.n - col0 < BS ? c.n - col0 : BS);
+  const bool full = nrow == BS && ncol == BS;
 
   // optional per-phase SM-cycle counts (trace): Dbuf wait, operand-chunk
   // waits, predecessor-tile wait; start to end of the relaxation, whole task
@@ -153,10 +155,15 @@ __device__ __noinline__ bool ws_minplus(TileCtx<T> c, int ti, int tj, bool fast,
   bool neg = false;
   if (fast) {
     uint32_t acc[TM][TM];
+    int32_t omax = 0;
 #pragma unroll
     for (int m = 0; m < TM; ++m)
 #pragma unroll
-      for (int nn = 0; nn < TM; ++nn) acc[m][nn] = kInt ? key_of<BS>((int32_t)old[m][nn]) : 0u;
+      for (int nn = 0; nn < TM; ++nn) {
+        acc[m][nn] = kInt ? key_of<BS>((int32_t)old[m][nn]) : 0u;
+        omax = max(omax, (int32_t)old[m][nn]);
+      }
+    const bool clamped = omax >= K::CAP;  // some old value's key is the clamp
     for (int ch = 0; ch < C::NC; ++ch) {
       const unsigned st = pc.chunk & 1;
       const long long w0 = tr ? clock64() : 0;
@@ -172,11 +179,12 @@ __device__ __noinline__ bool ws_minplus(TileCtx<T> c, int ti, int tj, bool fast,
       ++pc.chunk;
     }
     const long long t_c = tr ? clock64() : 0;
-    if (!mbar_wait(&wb->p_full, pc.p & 1, c.status, c.abort_flag, c.timeout_ns)) return false;
     if (tr) {
-      tr[7] = cyc20(t_b - t_a) | (cyc20(cw) << 20) | (cyc20(clock64() - t_c) << 40);
+      tr[7] = cyc20(t_b - t_a) | (cyc20(cw) << 20);
       tr[8] = (uint64_t)(t_c - t_a);
     }
+    // predecessors as "via k" codes: k = r*BS + code - 1
+    const int32_t via0 = via_code((int64_t)c.r * BS - 1);  // via_code(k) = via0 - code
     // most tasks of later rounds improve nothing in a warp's 16 x 128 rows:
     // one OR over the codes and a vote skip the epilogue
     uint32_t any = 0;
@@ -185,14 +193,9 @@ __device__ __noinline__ bool ws_minplus(TileCtx<T> c, int ti, int tj, bool fast,
 #pragma unroll
       for (int nn = 0; nn < TM; ++nn) any |= acc[m][nn];
     if (__any_sync(0xffffffffu, (any & K::MASK) != 0)) {
-      if (nrow == BS && ncol == BS) {
-        // D: a 16-byte vector wherever one of its G entries improved, the
-        // others rewritten unchanged.  An improved entry is a sum of operands
-        // below CAP and decodes exactly; so does an unchanged one unless its
-        // key is the clamp (old value CAP or more: INF or a large finite
-        // one), and a group holding such a key writes its improved entries
-        // one by one.  P: the improved entries only.
-        constexpr uint32_t kClampKey = (uint32_t)K::CAP << K::KB;
+      if (full && !__any_sync(0xffffffffu, clamped)) {
+        // no clamped key in the warp: every key decodes exactly; a group of
+        // G entries with an improvement is stored as one 16-byte vector
 #pragma unroll
         for (int m = 0; m < TM; ++m) {
           const int lr = Gm::idx(ty, m);
@@ -200,40 +203,34 @@ __device__ __noinline__ bool ws_minplus(TileCtx<T> c, int ti, int tj, bool fast,
           for (int g = 0; g < Gm::NG; ++g) {
             const int lc0 = g * Gm::SPAN + tx * G;
             uint32_t cg = 0;
-            bool clamp = false;
             T dv[G];
 #pragma unroll
             for (int e = 0; e < G; ++e) {
               const uint32_t kv = acc[m][g * G + e];
               cg |= kv & K::MASK;
-              clamp |= kv == kClampKey;
               dv[e] = (T)(int32_t)(kv >> K::KB);
             }
-            if (cg) {
-              if (!clamp) vstore<G>(Drow + lr * c.ld + lc0, dv);
+            if (cg) vstore<G>(Drow + lr * c.ld + lc0, dv);
 #pragma unroll
-              for (int e = 0; e < G; ++e) {
-                const uint32_t code = acc[m][g * G + e] & K::MASK;
-                if (code) {
-                  if (clamp) Drow[lr * c.ld + lc0 + e] = dv[e];
-                  Prow[lr * c.ld + lc0 + e] = Pbuf[(code - 1) * BS + lc0 + e];
-                }
-              }
+            for (int e = 0; e < G; ++e) {
+              const int code = (int)(acc[m][g * G + e] & K::MASK);
+              if (code) Prow[lr * c.ld + lc0 + e] = via0 - code;
             }
           }
         }
       } else {
+        // improved entries one by one (a clamped key -- old value CAP or
+        // more, INF or a large finite one -- keeps its old value)
 #pragma unroll
         for (int m = 0; m < TM; ++m) {
           const int lr = Gm::idx(ty, m);
 #pragma unroll
           for (int nn = 0; nn < TM; ++nn) {
-            const uint32_t code = acc[m][nn] & K::MASK;
+            const int code = (int)(acc[m][nn] & K::MASK);
             const int lc = Gm::idx(tx, nn);
             if (code && lr < nrow && lc < ncol) {
-              const int32_t nv = (int32_t)(acc[m][nn] >> K::KB);
-              Drow[lr * c.ld + lc] = (T)nv;
-              Prow[lr * c.ld + lc] = Pbuf[(code - 1) * BS + lc];
+              Drow[lr * c.ld + lc] = (T)(int32_t)(acc[m][nn] >> K::KB);
+              Prow[lr * c.ld + lc] = via0 - code;
             }
           }
         }
@@ -260,11 +257,14 @@ __device__ __noinline__ bool ws_minplus(TileCtx<T> c, int ti, int tj, bool fast,
       ++pc.chunk;
     }
     const long long t_c = tr ? clock64() : 0;
-    if (!mbar_wait(&wb->p_full, pc.p & 1, c.status, c.abort_flag, c.timeout_ns)) return false;
+    if constexpr (!ViaPred<T>::kOn) {
+      if (!mbar_wait(&wb->p_full, pc.p & 1, c.status, c.abort_flag, c.timeout_ns)) return false;
+    }
     if (tr) {
       tr[7] = cyc20(t_b - t_a) | (cyc20(cw) << 20) | (cyc20(clock64() - t_c) << 40);
       tr[8] = (uint64_t)(t_c - t_a);
     }
+    const int32_t via0 = via_code((int64_t)c.r * BS - 1);
 #pragma unroll
     for (int m = 0; m < TM; ++m) {
       const int lr = Gm::idx(ty, m);
@@ -273,16 +273,19 @@ __device__ __noinline__ bool ws_minplus(TileCtx<T> c, int ti, int tj, bool fast,
         const int lc = Gm::idx(tx, nn);
         if (arg[m][nn] && lr < nrow && lc < ncol) {
           Drow[lr * c.ld + lc] = old[m][nn];
-          Prow[lr * c.ld + lc] = Pbuf[(arg[m][nn] - 1) * BS + lc];
+          Prow[lr * c.ld + lc] =
+              ViaPred<T>::kOn ? via0 - arg[m][nn] : Pbuf[(arg[m][nn] - 1) * BS + lc];
           neg |= (row0 + lr == col0 + lc) && old[m][nn] < T(0);
         }
       }
     }
   }
   if (tr) tr[8] |= (uint64_t)(clock64() - t_a) << 32;  // whole task
-  __syncwarp();
-  if (lane == 0) mbar_arrive(&wb->p_empty);
-  ++pc.p;
+  if constexpr (!ViaPred<T>::kOn) {
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&wb->p_empty);
+    ++pc.p;
+  }
   if (neg) atomicOr(c.status, kStNegCycle);
   return true;
 }
@@ -293,7 +296,7 @@ __device__ bool compute_task(const Args<T>& a, const fwh::Task& k, bool fast, un
                              WsBars* wb, CtaScratch* cs, PipeCnt& pc, uint64_t* tr) {
   using L = WsLayout<LBS>;
   if (k.type == 3) {
-    const TileCtx<T> ctx{a.D, a.P, a.n, a.ld, a.status, a.abort_flag, a.timeout_ns};
+    const TileCtx<T> ctx{a.D, a.P, a.n, a.ld, k.r, a.status, a.abort_flag, a.timeout_ns};
     return ws_minplus<T, BS, LBS>(ctx, k.ti, k.tj, fast, smem, wb, pc, tr);
   }
   // Pivot and panel tasks overwrite the ring and Dbuf from their first
@@ -459,13 +462,15 @@ __device__ void issue_operands(const Args<T>& a, const fwh::Task& k, bool fast, 
     }
     ++pc.chunk;
   }
-  // predecessor tile of the row panel snapshot
-  if (lane == 0) {
-    mbar_wait(&wb->p_empty, (pc.p & 1) ^ 1, a.status, a.abort_flag, a.timeout_ns);
-    mbar_expect_tx(&wb->p_full, (unsigned)C::kTile);
-    bulk_g2s(smem + L::p_off(), a.rowP + toffB, (unsigned)C::kTile, &wb->p_full);
+  // predecessor tile of the row panel snapshot (fp32; int32 records "via" codes)
+  if constexpr (!ViaPred<T>::kOn) {
+    if (lane == 0) {
+      mbar_wait(&wb->p_empty, (pc.p & 1) ^ 1, a.status, a.abort_flag, a.timeout_ns);
+      mbar_expect_tx(&wb->p_full, (unsigned)C::kTile);
+      bulk_g2s(smem + L::p_off(), a.rowP + toffB, (unsigned)C::kTile, &wb->p_full);
+    }
+    ++pc.p;
   }
-  ++pc.p;
 }
 
 // Optional per-task trace (sampled tasks): 10 words per entry.
