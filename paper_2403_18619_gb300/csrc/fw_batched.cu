@@ -274,7 +274,7 @@ fw_status plan_build(fw_batched_plan* p) {
       cudaMemcpy(p->d_bs, p->bs.data(), (size_t)B * 4, cudaMemcpyHostToDevice) != cudaSuccess)
     return FW_ERR_CUDA;
 
-  const size_t smem = fwk::WsLayout<128>::bytes();
+  const size_t smem = fwk::WsLayout<128, T>::bytes();
   auto kern = fwk::k_batched_ws<T>;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess)
@@ -317,7 +317,7 @@ cudaError_t enqueue(fw_batched_plan* p, cudaStream_t s) {
   cudaLaunchConfig_t lc{};
   lc.gridDim = dim3((unsigned)p->grid);
   lc.blockDim = dim3(fwk::kWsThreads);
-  lc.dynamicSmemBytes = fwk::WsLayout<128>::bytes();
+  lc.dynamicSmemBytes = fwk::WsLayout<128, T>::bytes();
   lc.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;

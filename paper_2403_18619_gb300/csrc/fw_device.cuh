@@ -122,6 +122,23 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned phase) {
   return ok != 0;
 }
 
+// The same with a suspend-time hint (ns): a waiting thread sleeps until the
+// phase completes or the hint expires instead of re-polling at the hardware's
+// own, shorter interval.  Re-polling is not free: the producer warp shares an
+// SM sub-partition's issue slots and ALU pipe with two compute warps, and its
+// polls measurably slowed them.
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* bar, unsigned phase,
+                                                    unsigned hint_ns) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(phase), "r"(hint_ns)
+      : "memory");
+  return ok != 0;
+}
+
 // Barrier over the 256 compute threads (warps 0-7).  In kernels that add a
 // producer warp, that warp does not take part; in 256-thread kernels this is
 // the whole CTA.
@@ -1297,16 +1314,37 @@ __global__ void __launch_bounds__(256) k_init_pred(const T* __restrict__ D, int3
 }
 
 // Final pass of an int32 solve: every via code becomes the last hop its chain
-// ends in (see ViaPred).  In place: a concurrent reader of an entry sees
-// either its via code or the last hop that code resolves to, and follows
-// either to the same end.
+// ends in (see ViaPred).  A chain stays in its column, so the matrix is swept
+// in slabs of kResolveSlab columns, every CTA walking the slabs in the same
+// order: the random reads of a chain then hit the L2-resident slab instead of
+// DRAM.  Each warp takes one row segment of the slab (a 16-byte vector per
+// lane).  In place: a concurrent reader of an entry sees either its via code
+// or the last hop that code resolves to, and follows either to the same end.
+constexpr int kResolveSlab = 128;
 static __global__ void __launch_bounds__(256) k_resolve_pred(int32_t* P, int64_t n, int64_t ld) {
-  const int64_t total = n * n;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = e / n, j = e - i * n;
-    const int32_t p = P[i * ld + j];
-    if (p <= -2) P[i * ld + j] = resolve_pred(p, P, ld, j);
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t c0 = 0; c0 < n; c0 += kResolveSlab) {
+    const int64_t j = c0 + lane * 4;
+    if (j >= n) continue;
+    for (int64_t i = warp; i < n; i += nwarps) {
+      int32_t* row = P + i * ld;
+      if (j + 4 <= n) {
+        int4 v = *reinterpret_cast<int4*>(row + j);
+        if (min(min(v.x, v.y), min(v.z, v.w)) >= -1) continue;  // no via code here
+        v.x = resolve_pred(v.x, P, ld, j);
+        v.y = resolve_pred(v.y, P, ld, j + 1);
+        v.z = resolve_pred(v.z, P, ld, j + 2);
+        v.w = resolve_pred(v.w, P, ld, j + 3);
+        *reinterpret_cast<int4*>(row + j) = v;
+      } else {
+        for (int64_t jj = j; jj < n; ++jj) {
+          const int32_t p = row[jj];
+          if (p <= -2) row[jj] = resolve_pred(p, P, ld, jj);
+        }
+      }
+    }
   }
 }
 

@@ -43,15 +43,17 @@ __host__ __device__ inline Task task_L(int R, int r, int64_t l) {
   return ((l - 1) & 1) ? Task{3, r, jj, r + 1} : Task{3, r, r + 1, jj};
 }
 __host__ __device__ inline Task task_rest(int R, int r, int64_t u) {
+  // u < R^2 <= 2^20: 32-bit arithmetic
+  const unsigned uu = (unsigned)u;
   if (r + 1 < R) {
-    const int w = R - 2;
-    int i = (int)(u / w), j = (int)(u % w);
+    const unsigned w = (unsigned)(R - 2);
+    int i = (int)(uu / w), j = (int)(uu - (unsigned)i * w);
     i = i < r ? i : i + 2;
     j = j < r ? j : j + 2;
     return Task{3, r, i, j};
   }
-  const int w = R - 1;
-  int i = (int)(u / w), j = (int)(u % w);
+  const unsigned w = (unsigned)(R - 1);
+  int i = (int)(uu / w), j = (int)(uu - (unsigned)i * w);
   i = i < r ? i : i + 1;
   j = j < r ? j : j + 1;
   return Task{3, r, i, j};

@@ -79,7 +79,7 @@ cudaError_t run(T* D, int32_t* P, int64_t n, int64_t ld, unsigned char* base, in
   k_init_pred<T><<<(int)blocks, 256, 0, s>>>(D, P, n, ld);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
 
-  const size_t smem = WsLayout<BS>::bytes();
+  const size_t smem = WsLayout<BS, T>::bytes();
   auto kern = k_persistent_ws<T, BS>;
   if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
       cudaSuccess)

@@ -86,7 +86,7 @@ cudaError_t launch_bs(T* D, int32_t* P, int64_t n, int64_t ld, const fwh::SolveW
     }
   } else {
     auto kern = k_persistent_ws<T, BS>;
-    const size_t wsmem = WsLayout<BS>::bytes();
+    const size_t wsmem = WsLayout<BS, T>::bytes();
     static int occ = -1;
     if (occ < 0) {
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsmem);

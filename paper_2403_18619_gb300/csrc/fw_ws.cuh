@@ -8,11 +8,11 @@
 //     tasks into shared memory with TMA bulk copies while the compute warps
 //     work on the previous task:
 //       - the tile's own D block (one bulk copy per row)          -> Dbuf
-//       - the A and B panel snapshots, 32 k-steps per chunk       -> 2-stage ring
+//       - the A and B panel snapshots, 64 (fp32: 32) k-steps per chunk -> 2-stage ring
 //       - the predecessor tile of the B panel (for the epilogue)  -> Pbuf
 //   * The compute warps relax (min-plus over the chunks) and store improved
-//     entries; pivot and panel tasks are run by them alone, using the ring and
-//     Dbuf as scratch (the producer waits until such a task is published).
+//     entries; pivot and panel tasks are run by them alone, using the shared
+//     buffer as scratch (the producer waits until such a task is published).
 //   * The publisher sleeps on the compute warps' task-done barrier and
 //     publishes each finished tile (the GPU-scope release), so that neither the
 //     compute warps nor the producer wait on that fence.
@@ -34,27 +34,36 @@ namespace fwk {
 // thread (ptxas derives this from the launch bounds).
 constexpr int kWsThreads = kThreads + 64;
 constexpr int kPubDepth = 4;  // tasks handed to the compute warps but not yet published
-constexpr int kCK = 32;       // k-steps per streamed chunk
 
-// Operand sizes of a task with block size BS.
-template <int BS>
+// Operand chunks of a task with block size BS: CK k-steps of A and of B.
+// int32 streams 64-step chunks (2 per task at BS = 128: fewer ring hand-offs);
+// fp32 keeps 32-step chunks and spends the saved space on the predecessor
+// snapshot tile of its epilogue.
+template <int BS, typename T>
 struct WsChunk {
-  static constexpr int NC = BS / kCK;                          // chunks per task
-  static constexpr size_t kChunkBytes = (size_t)kCK * BS * 4;  // one operand chunk
+  static constexpr int kCKmax = ViaPred<T>::kOn ? 64 : 32;
+  static constexpr int CK = BS < kCKmax ? BS : kCKmax;        // k-steps per chunk
+  static constexpr int NC = BS / CK;                          // chunks per task
+  static constexpr size_t kChunkBytes = (size_t)CK * BS * 4;  // one operand chunk
   static constexpr size_t kTile = (size_t)BS * BS * 4;
 };
 
-// Shared-memory layout sized for the largest block size LBS a launch runs.
-template <int LBS>
+// Shared-memory layout sized for the largest block size LBS a launch runs:
+// the 2-stage operand ring, the tile's own D (Dbuf) and, for fp32, the
+// row-panel predecessor snapshot (Pbuf); 192 KB for LBS = 128 either way.
+template <int LBS, typename T>
 struct WsLayout {
-  static constexpr size_t kStage = 2 * WsChunk<LBS>::kChunkBytes;  // A chunk + B chunk
+  static constexpr size_t kStage = 2 * WsChunk<LBS, T>::kChunkBytes;  // A chunk + B chunk
   static constexpr size_t kRing = 2 * kStage;
-  static constexpr size_t kTile = WsChunk<LBS>::kTile;
+  static constexpr size_t kTile = WsChunk<LBS, T>::kTile;
   __host__ __device__ static constexpr size_t ring_off() { return 0; }
   __host__ __device__ static constexpr size_t d_off() { return kRing; }
   __host__ __device__ static constexpr size_t p_off() { return kRing + kTile; }
-  __host__ __device__ static constexpr size_t bytes() { return kRing + 2 * kTile; }
-  static_assert(kRing >= kTile, "pivot/panel tasks use the ring as a full tile buffer");
+  __host__ __device__ static constexpr size_t bytes() {
+    return kRing + kTile + (ViaPred<T>::kOn ? 0 : kTile);
+  }
+  // pivot and panel tasks use the buffer from offset 0 as scratch (3 tiles)
+  static_assert(bytes() >= 3 * kTile, "scratch of pivot / panel tasks");
 };
 
 struct WsBars {
@@ -72,8 +81,8 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, int* s
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = globaltimer();
   for (int64_t it = 0; it < ((int64_t)1 << 26); ++it) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if ((it & 255) == 255 && globaltimer() - t0 > (uint64_t)timeout_ns) break;
+    if (mbar_try_wait_sleep(bar, parity, 20000u)) return true;
+    if ((it & 15) == 15 && globaltimer() - t0 > (uint64_t)timeout_ns) break;
   }
   atomicOr(status, kStTimeout);
   atomicExch(abort_flag, 1);
@@ -107,13 +116,13 @@ struct PipeCnt {
 // Remaining-tile task (phase 4 of round r, tile ti,tj).  Returns false if an
 // operand never arrived (the kernel then stops).
 template <typename T, int BS, int LBS>
-__device__ __noinline__ bool ws_minplus(TileCtx<T> c, int ti, int tj, bool fast,
+__device__ __forceinline__ bool ws_minplus(TileCtx<T> c, int ti, int tj, bool fast,
                                         unsigned char* smem, WsBars* wb, PipeCnt& pc,
                                         uint64_t* tr) {
   using Gm = Geo<BS>;
   using K = Keys<BS>;
-  using L = WsLayout<LBS>;
-  using C = WsChunk<BS>;
+  using L = WsLayout<LBS, T>;
+  using C = WsChunk<BS, T>;
   constexpr int TM = Gm::TM, G = Gm::G;
   constexpr bool kInt = Num<T>::kInt;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4, lane = tid & 31;
@@ -172,8 +181,8 @@ __device__ __noinline__ bool ws_minplus(TileCtx<T> c, int ti, int tj, bool fast,
         return false;
       if (tr) cw += clock64() - w0;
       const uint32_t* As = reinterpret_cast<const uint32_t*>(ring + st * L::kStage);
-      const uint32_t* Bs = As + kCK * BS;
-      core_packed<BS, kCK>(As, Bs, acc, tx, ty);
+      const uint32_t* Bs = As + C::CK * BS;
+      core_packed<BS, C::CK>(As, Bs, acc, tx, ty);
       __syncwarp();
       if (lane == 0) mbar_arrive(&wb->chunk_empty[st]);
       ++pc.chunk;
@@ -250,8 +259,8 @@ __device__ __noinline__ bool ws_minplus(TileCtx<T> c, int ti, int tj, bool fast,
         return false;
       if (tr) cw += clock64() - w0;
       const T* As = reinterpret_cast<const T*>(ring + st * L::kStage);
-      const T* Bs = As + kCK * BS;
-      core_generic<BS, T, kCK>(As, Bs, old, arg, tx, ty, ch * kCK);
+      const T* Bs = As + C::CK * BS;
+      core_generic<BS, T, C::CK>(As, Bs, old, arg, tx, ty, ch * C::CK);
       __syncwarp();
       if (lane == 0) mbar_arrive(&wb->chunk_empty[st]);
       ++pc.chunk;
@@ -294,7 +303,7 @@ __device__ __noinline__ bool ws_minplus(TileCtx<T> c, int ti, int tj, bool fast,
 template <typename T, int BS, int LBS>
 __device__ bool compute_task(const Args<T>& a, const fwh::Task& k, bool fast, unsigned char* smem,
                              WsBars* wb, CtaScratch* cs, PipeCnt& pc, uint64_t* tr) {
-  using L = WsLayout<LBS>;
+  using L = WsLayout<LBS, T>;
   if (k.type == 3) {
     const TileCtx<T> ctx{a.D, a.P, a.n, a.ld, k.r, a.status, a.abort_flag, a.timeout_ns};
     return ws_minplus<T, BS, LBS>(ctx, k.ti, k.tj, fast, smem, wb, pc, tr);
@@ -306,9 +315,7 @@ __device__ bool compute_task(const Args<T>& a, const fwh::Task& k, bool fast, un
   if (k.type == 0) {
     task_pivot<T, BS>(a, k.r, smem + L::ring_off(), cs);
   } else {
-    // panel tasks put A in the ring region and B in Dbuf: contiguous, As + BS*BS = Dbuf
-    task_panel<T, BS>(a, k.r, k.type == 1 ? k.tj : k.ti, k.type == 1,
-                      smem + L::d_off() - (size_t)BS * BS * 4, cs);
+    task_panel<T, BS>(a, k.r, k.type == 1 ? k.tj : k.ti, k.type == 1, smem + L::ring_off(), cs);
   }
   bar_compute();
   return true;
@@ -412,8 +419,8 @@ __device__ __forceinline__ bool packed_ok(const Args<T>& a, const fwh::Task& k) 
 template <typename T, int BS, int LBS>
 __device__ void issue_operands(const Args<T>& a, const fwh::Task& k, bool fast, unsigned char* smem,
                                WsBars* wb, PipeCnt& pc, int lane) {
-  using L = WsLayout<LBS>;
-  using C = WsChunk<BS>;
+  using L = WsLayout<LBS, T>;
+  using C = WsChunk<BS, T>;
   fence_proxy_async();  // global data published by other CTAs, read by TMA below
   const int slot = k.r & 1;
   // the tile's own D block, one bulk copy per valid row
@@ -563,17 +570,18 @@ __device__ void ws_engine(const Src& src, unsigned char* smem, WsBars& wb, CtaSc
       if (lane == 0) {
         t_claim = globaltimer();
         const int64_t tt = atomicAdd(src.next, 1u);
-        if (tt < total && !ld_relaxed(src.abort_flag)) {
-          src.resolve(tt, g);
-          t = (int)tt;
-        }
+        if (tt < total && !ld_relaxed(src.abort_flag)) t = (int)tt;
       }
+      // lane 0 decodes the task; the others take it by shuffle
+      fwh::Task k{0, 0, 0, 0};
+      if (lane == 0 && t >= 0) k = src.resolve(t, g);
       t = __shfl_sync(0xffffffffu, t, 0);
       g = __shfl_sync(0xffffffffu, g, 0);
-      fwh::Task k{0, 0, 0, 0};
+      k.type = __shfl_sync(0xffffffffu, k.type, 0);
+      k.r = __shfl_sync(0xffffffffu, k.r, 0);
+      k.ti = __shfl_sync(0xffffffffu, k.ti, 0);
+      k.tj = __shfl_sync(0xffffffffu, k.tj, 0);
       if (t >= 0) {
-        int g2 = 0;
-        k = src.resolve(t, g2);
         if (!wait_deps(src.args(g), k, lane)) t = -1;
       }
       if (lane == 0) {
@@ -626,7 +634,7 @@ __device__ void ws_engine(const Src& src, unsigned char* smem, WsBars& wb, CtaSc
         });
       } else {
         if (lane == 0) {
-          // pivot / panel tasks use the ring and Dbuf as scratch: wait until
+          // pivot / panel tasks use the shared buffer as scratch: wait until
           // this task has been published (its publication-queue slot frees up)
           mbar_wait(&wb.pub_empty[pq], (((ipub - 1) / kPubDepth) & 1), src.status,
                     src.abort_flag, src.timeout_ns);
