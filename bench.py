@@ -40,9 +40,9 @@ BS = 128
 SAMPLE_N = 2048          # CPU baseline: leading 2048-vertex induced subgraph
 
 
-def workload_name():
+def workload_name(n=N_FULL):
     return ("blocked FW, n=%d complete digraph minus 10%% edges, int32 weights U[1,1e4], "
-            "INF=2^29, dist+pred (flag-scheduled persistent driver)" % N_FULL)
+            "INF=2^29, dist+pred (flag-scheduled persistent driver)" % n)
 
 
 # ------------------------------------------------------------------ clocks ---
@@ -393,7 +393,7 @@ def run_gpu(args):
         "vs_baseline": None,
         "dtype": "int32",
         "data": "synthetic",
-        "config": {"workload": workload_name(), "n": n, "edge_p": P_EDGE, "weights": [LO, HI],
+        "config": {"workload": workload_name(n), "n": n, "edge_p": P_EDGE, "weights": [LO, HI],
                    "bs": args.bs, "driver": "phased" if args.driver == 2 else "persistent",
                    "parallelism": "replicas x%d" % world,
                    "l2": "no flush: 8 GiB of dist+pred per step, far above the 129 MB L2"},
