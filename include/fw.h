@@ -99,7 +99,9 @@ typedef struct fw_options {
                                  Min-plus tasks add SM-cycle counts: column 7 = tile-load wait |
                                  operand-chunk waits << 20 | predecessor-tile wait << 40 (20 bits
                                  each, saturating), column 8 = cycles from task start to the end
-                                 of the relaxation | whole task << 32 */
+                                 of the relaxation | whole task << 32.  Pivot and panel tasks:
+                                 column 7 = operands loaded | relaxed << 32, column 8 = results
+                                 stored | whole task << 32 (SM cycles from the task's start) */
   int64_t trace_cap;
   int32_t trace_stride;
   int32_t tile_tma;           /* persistent driver: 1 (default) loads each remaining tile with one

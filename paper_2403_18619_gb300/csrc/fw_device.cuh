@@ -144,6 +144,13 @@ __device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* bar, unsigned phas
 // the whole CTA.
 __device__ __forceinline__ void bar_compute() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
 
+// SM-cycle stamps of the phases of the current pivot / panel task (thread 0
+// writes them; the persistent driver's optional trace reads them).
+static __shared__ long long t_stamp[4];
+__device__ __forceinline__ void stamp(int i) {
+  if (threadIdx.x == 0) t_stamp[i] = clock64();
+}
+
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
@@ -585,21 +592,22 @@ __device__ __forceinline__ void pivot_publish_next(uint32_t (&acc)[Geo<BS>::TM][
 
 // Packed-key pivot (int32, bounded entries).
 template <typename T, int BS>
-__device__ __noinline__ void pivot_packed(const Args<T>& a, int r, void* smem_raw) {
+__device__ __forceinline__ void pivot_packed(const Args<T>& a, int r, void* smem_raw,
+                                             const T (&d)[Geo<BS>::TM][Geo<BS>::TM],
+                                             const int32_t (&p)[Geo<BS>::TM][Geo<BS>::TM]) {
   using Gm = Geo<BS>;
   using K = Keys<BS>;
   constexpr int TM = Gm::TM, G = Gm::G, NG = Gm::NG;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  // shared memory: [0, BS^2) the step broadcasts, then (after the steps) nxt;
+  // [BS^2, 2 BS^2) val; [2 BS^2, 3 BS^2) the closed distances until stored
   uint32_t* rowK = reinterpret_cast<uint32_t*>(smem_raw);  // [2][BS]
   uint32_t* colK = rowK + 2 * BS;                          // [2][BS]
-  int32_t* nxt = reinterpret_cast<int32_t*>(colK + 2 * BS);  // [BS][BS], after the steps
-  int32_t* val = nxt + BS * BS;                              // [BS][BS]
+  int32_t* nxt = reinterpret_cast<int32_t*>(smem_raw);     // [BS][BS], after the steps
+  int32_t* val = nxt + BS * BS;                            // [BS][BS]
+  T* dst = reinterpret_cast<T*>(val + BS * BS);            // [BS][BS]
   uint32_t acc[TM][TM];
   {
-    T d[TM][TM];
-    int32_t p[TM][TM];
-    load_tile<BS>(d, a.D, a.n, a.ld, r, r, tx, ty, Num<T>::inf());
-    load_tile<BS>(p, a.P, a.n, a.ld, r, r, tx, ty, (int32_t)-1);
     // the old predecessors wait in shared memory (not in registers) during the steps
 #pragma unroll
     for (int mm = 0; mm < TM; ++mm)
@@ -609,6 +617,7 @@ __device__ __noinline__ void pivot_packed(const Args<T>& a, int r, void* smem_ra
         acc[mm][nn] = key_of<BS>((int32_t)d[mm][nn]);
       }
   }
+  stamp(1);
   // broadcast of step 0: row 0 and column 0 (owner thread row / column 0, register 0)
   if (ty == 0) {
 #pragma unroll
@@ -663,29 +672,26 @@ __device__ __noinline__ void pivot_packed(const Args<T>& a, int r, void* smem_ra
       });
     }
   });
-  // distances out first; then the chains of last steps.  Element (a, b) last
-  // improved at step kk takes the final last hop of (kk, b), whose own last
-  // improving step is earlier: walk each chain down to an element that never
-  // improved and take its old predecessor.
+  stamp(2);
+  // Chains of last steps: element (a, b) last improved at step kk takes the
+  // final last hop of (kk, b), whose own last improving step is earlier; walk
+  // each chain down to an element that never improved and take its old
+  // predecessor.  The closed distances wait in shared memory: global stores
+  // issued now would hold up the walk's shared loads behind them in the
+  // load/store queue when memory is busy.
+  bar_compute();  // nxt overwrites the last step's broadcast
 #pragma unroll
   for (int mm = 0; mm < TM; ++mm)
 #pragma unroll
-    for (int nn = 0; nn < TM; ++nn)
-      nxt[Gm::idx(ty, mm) * BS + Gm::idx(tx, nn)] = (int)(acc[mm][nn] & K::MASK) - 1;
-  {
-    T d[TM][TM];
-#pragma unroll
-    for (int mm = 0; mm < TM; ++mm)
-#pragma unroll
-      for (int nn = 0; nn < TM; ++nn) {
-        const int32_t v = (int32_t)(acc[mm][nn] >> K::KB);
-        d[mm][nn] = v == K::CAP ? Num<T>::inf() : (T)v;
-      }
-    pivot_store_dist<T, BS>(a, r, d, tx, ty);
-  }
+    for (int nn = 0; nn < TM; ++nn) {
+      const int e = Gm::idx(ty, mm) * BS + Gm::idx(tx, nn);
+      nxt[e] = (int)(acc[mm][nn] & K::MASK) - 1;
+      const int32_t v = (int32_t)(acc[mm][nn] >> K::KB);
+      dst[e] = v == K::CAP ? Num<T>::inf() : (T)v;
+    }
   bar_compute();
   constexpr int kWalk = 8;  // hops walked directly; longer chains fall back to jumping
-  int32_t p[TM][TM];
+  int32_t pr[TM][TM];
   bool unresolved = false;
 #pragma unroll
   for (int mm = 0; mm < TM; ++mm)
@@ -700,7 +706,7 @@ __device__ __noinline__ void pivot_packed(const Args<T>& a, int r, void* smem_ra
         k = nxt[k * BS + col];
       }
       unresolved |= k >= 0;
-      p[mm][nn] = val[x * BS + col];
+      pr[mm][nn] = val[x * BS + col];
     }
   if (bar_compute_or(unresolved)) {
     // pointer jumping: every round doubles the resolved chain length, and a
@@ -717,7 +723,7 @@ __device__ __noinline__ void pivot_packed(const Args<T>& a, int r, void* smem_ra
           if (k >= 0) {
             const int nkk = nxt[k * BS + col];
             nk[mm][nn] = nkk;
-            if (nkk < 0) p[mm][nn] = val[k * BS + col];
+            if (nkk < 0) pr[mm][nn] = val[k * BS + col];
           }
         }
       bar_compute();
@@ -728,7 +734,7 @@ __device__ __noinline__ void pivot_packed(const Args<T>& a, int r, void* smem_ra
           if (nk[mm][nn] == -2) continue;
           const int e = Gm::idx(ty, mm) * BS + Gm::idx(tx, nn);
           if (nk[mm][nn] < 0) {
-            val[e] = p[mm][nn];
+            val[e] = pr[mm][nn];
             nxt[e] = -1;
           } else {
             nxt[e] = nk[mm][nn];
@@ -739,9 +745,18 @@ __device__ __noinline__ void pivot_packed(const Args<T>& a, int r, void* smem_ra
 #pragma unroll
     for (int mm = 0; mm < TM; ++mm)
 #pragma unroll
-      for (int nn = 0; nn < TM; ++nn) p[mm][nn] = val[Gm::idx(ty, mm) * BS + Gm::idx(tx, nn)];
+      for (int nn = 0; nn < TM; ++nn) pr[mm][nn] = val[Gm::idx(ty, mm) * BS + Gm::idx(tx, nn)];
   }
-  pivot_store_pred<T, BS>(a, r, p, tx, ty);
+  stamp(3);
+  {
+    T dd[TM][TM];
+#pragma unroll
+    for (int mm = 0; mm < TM; ++mm)
+#pragma unroll
+      for (int nn = 0; nn < TM; ++nn) dd[mm][nn] = dst[Gm::idx(ty, mm) * BS + Gm::idx(tx, nn)];
+    pivot_store_dist<T, BS>(a, r, dd, tx, ty);
+  }
+  pivot_store_pred<T, BS>(a, r, pr, tx, ty);
 }
 
 // Eager pivot: compare and select per relaxation (fp32, large int32 entries).
@@ -754,6 +769,7 @@ __device__ __noinline__ void pivot_eager(const Args<T>& a, int r, void* smem_raw
   int32_t p[TM][TM];
   load_tile<BS>(d, a.D, a.n, a.ld, r, r, tx, ty, Num<T>::inf());
   load_tile<BS>(p, a.P, a.n, a.ld, r, r, tx, ty, (int32_t)-1);
+  stamp(1);
   T* rowD = reinterpret_cast<T*>(smem_raw);  // [2][BS]
   int32_t* rowP = reinterpret_cast<int32_t*>(rowD + 2 * BS);
   T* colD = reinterpret_cast<T*>(rowP + 2 * BS);
@@ -798,6 +814,8 @@ __device__ __noinline__ void pivot_eager(const Args<T>& a, int r, void* smem_raw
       }
     }
   }
+  stamp(2);
+  stamp(3);
   pivot_store_dist<T, BS>(a, r, d, tx, ty);
   pivot_store_pred<T, BS>(a, r, p, tx, ty);
 }
@@ -819,25 +837,28 @@ __device__ __noinline__ void task_pivot(const Args<T>& a, int r, void* smem_raw,
   using Gm = Geo<BS>;
   using K = Keys<BS>;
   constexpr int TM = Gm::TM;
-  bool fast = false;
+  stamp(0);
   if constexpr (Num<T>::kInt) {
     // every value formed in the closure is a path of at most BS segments of
-    // current entries; keep twice that below CAP
+    // current entries; keep twice that below CAP.  The tile is loaded once,
+    // distances and predecessors together (one memory round trip).
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     T d[TM][TM];
+    int32_t p[TM][TM];
     load_tile<BS>(d, a.D, a.n, a.ld, r, r, tx, ty, Num<T>::inf());
+    load_tile<BS>(p, a.P, a.n, a.ld, r, r, tx, ty, (int32_t)-1);
     int bnd = 0, dummy = 0;
 #pragma unroll
     for (int mm = 0; mm < TM; ++mm)
 #pragma unroll
       for (int nn = 0; nn < TM; ++nn) bnd = max(bnd, bound_of<BS>(d[mm][nn]));
     block_max2(bnd, dummy, cs);
-    fast = a.packed && (int64_t)bnd * 2 * BS < (int64_t)K::CAP;
+    if (a.packed && (int64_t)bnd * 2 * BS < (int64_t)K::CAP) {
+      pivot_packed<T, BS>(a, r, smem_raw, d, p);
+      return;
+    }
   }
-  if (fast)
-    pivot_packed<T, BS>(a, r, smem_raw);
-  else
-    pivot_eager<T, BS>(a, r, smem_raw);
+  pivot_eager<T, BS>(a, r, smem_raw);
 }
 
 // ------------------------------------------------------------- phase 2/3 ----
@@ -866,23 +887,32 @@ __device__ __forceinline__ void load_buf(T (&v)[Geo<BS>::TM][Geo<BS>::TM], const
 template <int BS>
 __device__ __forceinline__ void stage_tile_i32(int32_t* dst, const int32_t* M, int64_t n, int64_t ld,
                                                int ti, int tj, const int32_t* buf) {
-  constexpr int V = BS / 4;  // 16-byte vectors per row
-  for (int q = threadIdx.x; q < BS * V; q += kThreads) {
+  constexpr int V = BS / 4;                 // 16-byte vectors per row
+  constexpr int NQ = BS * V / kThreads;     // vectors per thread
+  static_assert(NQ * kThreads == BS * V, "tile not divisible among the threads");
+  // every load first, then every store: one memory round trip, not NQ
+  int4 v[NQ];
+#pragma unroll
+  for (int u = 0; u < NQ; ++u) {
+    const int q = (int)threadIdx.x + u * kThreads;
     const int row = q / V, c4 = (q % V) * 4;
-    int4 v;
     if (!M) {
-      v = __ldcg(reinterpret_cast<const int4*>(buf + row * BS + c4));
+      v[u] = __ldcg(reinterpret_cast<const int4*>(buf + row * BS + c4));
     } else {
       const int64_t gi = (int64_t)ti * BS + row, gj = (int64_t)tj * BS + c4;
-      v = make_int4(-1, -1, -1, -1);
+      v[u] = make_int4(-1, -1, -1, -1);
       if (gi < n && gj < n) {
-        v = __ldcg(reinterpret_cast<const int4*>(M + gi * ld + gj));
-        if (gj + 1 >= n) v.y = -1;
-        if (gj + 2 >= n) v.z = -1;
-        if (gj + 3 >= n) v.w = -1;
+        v[u] = __ldcg(reinterpret_cast<const int4*>(M + gi * ld + gj));
+        if (gj + 1 >= n) v[u].y = -1;
+        if (gj + 2 >= n) v[u].z = -1;
+        if (gj + 3 >= n) v[u].w = -1;
       }
     }
-    *reinterpret_cast<int4*>(dst + row * BS + c4) = v;
+  }
+#pragma unroll
+  for (int u = 0; u < NQ; ++u) {
+    const int q = (int)threadIdx.x + u * kThreads;
+    *reinterpret_cast<int4*>(dst + (q / V) * BS + (q % V) * 4) = v[u];
   }
 }
 
@@ -1006,6 +1036,7 @@ __device__ __noinline__ int panel_packed(const Args<T>& a, int r, int t,
       }
   }
   core_packed<BS>(As, Bs, acc, tx, ty);
+  stamp(2);
   // every finite value is below CAP here, so a key decodes exactly and its
   // clamp value can only mean INF
   int nb = 0;
@@ -1068,6 +1099,7 @@ __device__ __noinline__ int panel_eager(const Args<T>& a, int r, int t, const T*
 #pragma unroll
     for (int nn = 0; nn < TM; ++nn) code[m][nn] = 0;
   core_generic<BS, T>(As, Bs, s, code, tx, ty);
+  stamp(2);
   int nb = 0;
 #pragma unroll
   for (int g = 0; g < Gm::NG; ++g) {
@@ -1115,6 +1147,7 @@ __device__ __noinline__ void task_panel(const Args<T>& a, int r, int t, bool is_
   uint32_t* As = reinterpret_cast<uint32_t*>(smem_raw);
   uint32_t* Bs = As + BS * BS;
   int32_t* Ps = reinterpret_cast<int32_t*>(Bs + BS * BS);
+  stamp(0);
 
   // predecessor source, staged (its loads overlap the operand loads below)
   if (is_row)
@@ -1174,6 +1207,7 @@ __device__ __noinline__ void task_panel(const Args<T>& a, int r, int t, bool is_
     }
   }
   bar_compute();
+  stamp(1);
 
   const T* Ast = reinterpret_cast<const T*>(As);
   const T* Bst = reinterpret_cast<const T*>(Bs);
@@ -1181,6 +1215,7 @@ __device__ __noinline__ void task_panel(const Args<T>& a, int r, int t, bool is_
                           : panel_eager<T, BS, true>(a, r, t, Ast, Bst, Ps))
                   : (fast ? panel_packed<T, BS, false>(a, r, t, As, Bs, Ps)
                           : panel_eager<T, BS, false>(a, r, t, Ast, Bst, Ps));
+  stamp(3);
   int dummy = 0;
   if constexpr (kInt) {
     block_max2(nb, dummy, cs);

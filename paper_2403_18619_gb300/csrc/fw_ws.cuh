@@ -318,6 +318,13 @@ __device__ bool compute_task(const Args<T>& a, const fwh::Task& k, bool fast, un
     task_panel<T, BS>(a, k.r, k.type == 1 ? k.tj : k.ti, k.type == 1, smem + L::ring_off(), cs);
   }
   bar_compute();
+  if (tr) {
+    // pivot: loads | steps ; predecessors resolved | end.  panel: operands
+    // staged | relaxed ; stored | end (SM cycles from the task's start)
+    const long long t0 = t_stamp[0], t_end = clock64();
+    tr[7] = (uint64_t)(t_stamp[1] - t0) | ((uint64_t)(t_stamp[2] - t0) << 32);
+    tr[8] = (uint64_t)(t_stamp[3] - t0) | ((uint64_t)(t_end - t0) << 32);
+  }
   return true;
 }
 
