@@ -693,21 +693,38 @@ __device__ __forceinline__ void pivot_packed(const Args<T>& a, int r, void* smem
   constexpr int kWalk = 8;  // hops walked directly; longer chains fall back to jumping
   int32_t pr[TM][TM];
   bool unresolved = false;
+  {
+    // all of a thread's chains advance one hop at a time, so that the
+    // dependent shared loads of different chains overlap; c is each chain's
+    // current row (ended when its nxt entry is negative)
+    int c[TM][TM];
 #pragma unroll
-  for (int mm = 0; mm < TM; ++mm)
+    for (int mm = 0; mm < TM; ++mm)
 #pragma unroll
-    for (int nn = 0; nn < TM; ++nn) {
-      const int col = Gm::idx(tx, nn);
-      int x = Gm::idx(ty, mm);
-      int k = nxt[x * BS + col];
+      for (int nn = 0; nn < TM; ++nn) c[mm][nn] = Gm::idx(ty, mm);
+    bool moved = true;
 #pragma unroll 1
-      for (int hop = 0; hop < kWalk && k >= 0; ++hop) {
-        x = k;
-        k = nxt[k * BS + col];
-      }
-      unresolved |= k >= 0;
-      pr[mm][nn] = val[x * BS + col];
+    for (int hop = 0; hop < kWalk && moved; ++hop) {
+      moved = false;
+#pragma unroll
+      for (int mm = 0; mm < TM; ++mm)
+#pragma unroll
+        for (int nn = 0; nn < TM; ++nn) {
+          const int nx = nxt[c[mm][nn] * BS + Gm::idx(tx, nn)];
+          if (nx >= 0) {
+            c[mm][nn] = nx;
+            moved = true;
+          }
+        }
+      moved = __any_sync(0xffffffffu, moved);
     }
+    // a warp that still moved on its last allowed hop may hold longer chains
+    unresolved = moved;
+#pragma unroll
+    for (int mm = 0; mm < TM; ++mm)
+#pragma unroll
+      for (int nn = 0; nn < TM; ++nn) pr[mm][nn] = val[c[mm][nn] * BS + Gm::idx(tx, nn)];
+  }
   if (bar_compute_or(unresolved)) {
     // pointer jumping: every round doubles the resolved chain length, and a
     // chain is at most BS long (its steps strictly decrease)
