@@ -283,6 +283,47 @@ def bench_backward(fw, args):
             "speedup_vs_one_launch_per_graph": t_single / (fwd + bwd)}
 
 
+def bench_configs(fw, args):
+    """The other single-graph workloads: n = 1024 complete digraph, int32
+    U[1,100], BS = 32 (launch / latency-bound), and n = 8192, p = 0.5, as fp32
+    (0,1] and as int32 U[1,1000], each against its own measured peak."""
+    import torch
+    import graphgen.device as gdev
+    out = {}
+    peaks = {fw.FW_I32: fw.fw_peak_probe(fw.FW_I32)[0], fw.FW_F32: fw.fw_peak_probe(fw.FW_F32)[0]}
+    cases = [("n1024_i32_bs32", 1024, fw.FW_I32, 1.0, 32, dict(lo=1, hi=100), 1),
+             ("n8192_i32_p0.5", 8192, fw.FW_I32, 0.5, 0, dict(lo=1, hi=1000), 2),
+             ("n8192_f32_p0.5", 8192, fw.FW_F32, 0.5, 0, dict(kind=0), 2)]
+    for name, n, dt, p, bs, gen, seed in cases:
+        ld = fw.padded(n)
+        tdt = torch.int32 if dt == fw.FW_I32 else torch.float32
+        W = torch.empty((n, ld), dtype=tdt, device="cuda")
+        if dt == fw.FW_I32:
+            gdev.fill_i32(W[:, :n], seed=seed, p=p, **gen)
+        else:
+            gdev.fill_f32(W[:, :n], seed=seed, p=p, **gen)
+        D = torch.empty_like(W)
+        P = torch.empty((n, ld), dtype=torch.int32, device="cuda")
+        opt = fw.Options.default(bs=bs)
+        steps = max(3, args.steps)
+        ts = []
+        for i in range(2 + steps):
+            D.copy_(W)
+            a, b = _events(2)
+            a.record()
+            fw.fw_solve_ex(D[:, :n], P[:, :n], opt)
+            b.record()
+            fw.fw_sync_status()
+            if i >= 2:
+                ts.append(a.elapsed_time(b))
+        t = sorted(ts)[len(ts) // 2]
+        rps = n ** 3 / (t * 1e-3)
+        out[name] = {"ms_median": t, "relax_per_s": rps, "frac_of_peak": rps / peaks[dt],
+                     "peak_relax_per_s": peaks[dt], "steps": steps}
+        del W, D, P
+    return out
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -412,6 +453,7 @@ def run_gpu(args):
     if not args.no_extras and world == 1:
         line["batched"] = bench_batched(fw, args)
         line["backward"] = bench_backward(fw, args)
+        line["configs"] = bench_configs(fw, args)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)
