@@ -286,15 +286,17 @@ def bench_backward(fw, args):
 def bench_configs(fw, args):
     """The other single-graph workloads: n = 1024 complete digraph, int32
     U[1,100], BS = 32 (launch / latency-bound), and n = 8192, p = 0.5, as fp32
-    (0,1] and as int32 U[1,1000], each against its own measured peak."""
+    (0,1] (with and without predecessors) and as int32 U[1,1000], each
+    against its own measured peak."""
     import torch
     import graphgen.device as gdev
     out = {}
     peaks = {fw.FW_I32: fw.fw_peak_probe(fw.FW_I32)[0], fw.FW_F32: fw.fw_peak_probe(fw.FW_F32)[0]}
-    cases = [("n1024_i32_bs32", 1024, fw.FW_I32, 1.0, 32, dict(lo=1, hi=100), 1),
-             ("n8192_i32_p0.5", 8192, fw.FW_I32, 0.5, 0, dict(lo=1, hi=1000), 2),
-             ("n8192_f32_p0.5", 8192, fw.FW_F32, 0.5, 0, dict(kind=0), 2)]
-    for name, n, dt, p, bs, gen, seed in cases:
+    cases = [("n1024_i32_bs32", 1024, fw.FW_I32, 1.0, 32, dict(lo=1, hi=100), 1, True),
+             ("n8192_i32_p0.5", 8192, fw.FW_I32, 0.5, 0, dict(lo=1, hi=1000), 2, True),
+             ("n8192_f32_p0.5", 8192, fw.FW_F32, 0.5, 0, dict(kind=0), 2, True),
+             ("n8192_f32_p0.5_distance_only", 8192, fw.FW_F32, 0.5, 0, dict(kind=0), 2, False)]
+    for name, n, dt, p, bs, gen, seed, with_pred in cases:
         ld = fw.padded(n)
         tdt = torch.int32 if dt == fw.FW_I32 else torch.float32
         W = torch.empty((n, ld), dtype=tdt, device="cuda")
@@ -311,7 +313,7 @@ def bench_configs(fw, args):
             D.copy_(W)
             a, b = _events(2)
             a.record()
-            fw.fw_solve_ex(D[:, :n], P[:, :n], opt)
+            fw.fw_solve_ex(D[:, :n], P[:, :n] if with_pred else None, opt)
             b.record()
             fw.fw_sync_status()
             if i >= 2:

@@ -119,7 +119,9 @@ const char* fw_status_string(fw_status s);
  * blocked algorithm of Sec. 2.3, Fig. 2).
  *   dist  device pointer, n x ld, dtype elements; holds the weights on entry
  *         and the distances on exit.
- *   pred  device pointer, n x ld int32, output only (may not alias dist).
+ *   pred  device pointer, n x ld int32, output only (may not alias dist); NULL
+ *         for a distance-only solve (no predecessor work at all; fp32 then
+ *         relaxes with an add and a min per step instead of compare+select).
  *   n     vertices, 1 <= n <= 131072.   ld  leading dimension, ld >= n, ld % 4 == 0.
  *   dtype FW_I32 or FW_F32.
  * Returns FW_OK once the work is enqueued.
@@ -133,7 +135,8 @@ fw_status fw_solve_ex(void* dist, int32_t* pred, int64_t n, int64_t ld, fw_dtype
 /*
  * fw_solve_host: the same solve on HOST buffers.  dist_host (n x ld, dtype)
  * is copied to the device, solved, and dist_host / pred_host (n x ld int32)
- * receive the results.  Pinned host memory gives full copy bandwidth; pageable
+ * receive the results (pred_host NULL: distances only).  Pinned host memory
+ * gives full copy bandwidth; pageable
  * memory works too.  Synchronous: returns after the results are on the host,
  * with any device-side error (as fw_sync_status would report it).  Device
  * buffers are cached per (device, stream) like the workspace.
@@ -156,7 +159,8 @@ typedef struct fw_batched_plan fw_batched_plan;
 fw_status fw_batched_plan_create(fw_batched_plan** plan, const int64_t* n, const int64_t* ld,
                                  int64_t batch, fw_dtype dtype, const fw_options* opt);
 
-/* dist[b], pred[b]: HOST arrays of device pointers (batch entries each). */
+/* dist[b], pred[b]: HOST arrays of device pointers (batch entries each); pred
+ * NULL (or a NULL entry) solves for distances only. */
 fw_status fw_solve_batched(fw_batched_plan* plan, void* const* dist, int32_t* const* pred,
                            void* stream);
 

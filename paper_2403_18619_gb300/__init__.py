@@ -148,19 +148,27 @@ def _matrix(t, name):
 
 
 def fw_solve(dist, pred, stream=None) -> None:
-    """fw_solve on CUDA tensors (n x n views, leading dimension = row stride)."""
+    """fw_solve on CUDA tensors (n x n views, leading dimension = row stride);
+    pred=None solves for distances only."""
     dp, n, ld = _matrix(dist, "dist")
-    pp, n2, ld2 = _matrix(pred, "pred")
-    if n2 != n or ld2 != ld:
-        raise ValueError("dist and pred must have the same shape and row stride")
+    pp = _pred_arg(pred, n, ld)
     check(load().fw_solve(dp, pp, n, ld, _dtype_code(dist), _stream_ptr(stream)), "fw_solve")
 
 
-def fw_solve_ex(dist, pred, options: Options | None = None, stream=None) -> None:
-    dp, n, ld = _matrix(dist, "dist")
+def _pred_arg(pred, n, ld):
+    """Device pointer of pred, or None for a distance-only solve."""
+    if pred is None:
+        return None
     pp, n2, ld2 = _matrix(pred, "pred")
     if n2 != n or ld2 != ld:
         raise ValueError("dist and pred must have the same shape and row stride")
+    return pp
+
+
+def fw_solve_ex(dist, pred, options: Options | None = None, stream=None) -> None:
+    """fw_solve_ex on CUDA tensors; pred=None solves for distances only."""
+    dp, n, ld = _matrix(dist, "dist")
+    pp = _pred_arg(pred, n, ld)
     o = ctypes.byref(options) if options is not None else None
     check(load().fw_solve_ex(dp, pp, n, ld, _dtype_code(dist), o, _stream_ptr(stream)),
           "fw_solve_ex")
@@ -170,9 +178,7 @@ def fw_solve_noalloc(dist, pred, stream=None) -> None:
     """fw_solve_noalloc on CUDA tensors: the solve without any device allocation
     (workspace in a fixed static device array; n <= 4096; synchronous)."""
     dp, n, ld = _matrix(dist, "dist")
-    pp, n2, ld2 = _matrix(pred, "pred")
-    if n2 != n or ld2 != ld:
-        raise ValueError("dist and pred must have the same shape and row stride")
+    pp = _pred_arg(pred, n, ld)
     check(load().fw_solve_noalloc(dp, pp, n, ld, _dtype_code(dist), _stream_ptr(stream)),
           "fw_solve_noalloc")
 
@@ -184,7 +190,7 @@ def fw_solve_host(dist: np.ndarray, pred: np.ndarray, options: Options | None = 
     if isinstance(dist, torch.Tensor):
         dptr, n, ld = dist.data_ptr(), dist.shape[0], dist.stride(0)
         code = _dtype_code(dist)
-        pptr = pred.data_ptr()
+        pptr = pred.data_ptr() if pred is not None else None
     else:
         if dist.ndim != 2 or dist.strides[1] != dist.itemsize:
             raise ValueError("dist must be a 2-D array with unit column stride")
@@ -192,7 +198,8 @@ def fw_solve_host(dist: np.ndarray, pred: np.ndarray, options: Options | None = 
         code = FW_I32 if dist.dtype == np.int32 else FW_F32 if dist.dtype == np.float32 else None
         if code is None:
             raise TypeError("dist must be int32 or float32")
-        dptr, pptr = dist.ctypes.data, pred.ctypes.data
+        dptr = dist.ctypes.data
+        pptr = pred.ctypes.data if pred is not None else None
     o = ctypes.byref(options) if options is not None else None
     check(load().fw_solve_host(dptr, pptr, n, ld, code, o, _stream_ptr(stream)), "fw_solve_host")
 
@@ -275,14 +282,17 @@ class BatchedPlan:
         self._pp = (ctypes.c_void_p * self.batch)()
 
     def solve(self, dists, preds, stream=None) -> None:
-        """dists/preds: sequences of CUDA tensors (n_b x n_b views) or raw device pointers."""
-        if len(dists) != self.batch or len(preds) != self.batch:
+        """dists/preds: sequences of CUDA tensors (n_b x n_b views) or raw device
+        pointers; preds=None solves every graph for distances only."""
+        if len(dists) != self.batch or (preds is not None and len(preds) != self.batch):
             raise ValueError("expected %d graphs" % self.batch)
-        for b, (d, p) in enumerate(zip(dists, preds)):
+        for b, d in enumerate(dists):
             self._dp[b] = d if isinstance(d, int) else d.data_ptr()
-            self._pp[b] = p if isinstance(p, int) else p.data_ptr()
-        check(load().fw_solve_batched(self._h, self._dp, self._pp, _stream_ptr(stream)),
-              "fw_solve_batched")
+        if preds is not None:
+            for b, p in enumerate(preds):
+                self._pp[b] = p if isinstance(p, int) else p.data_ptr()
+        check(load().fw_solve_batched(self._h, self._dp, self._pp if preds is not None else None,
+                                      _stream_ptr(stream)), "fw_solve_batched")
 
     def info(self):
         bs = np.zeros(self.batch, np.int32)
@@ -349,14 +359,18 @@ def solve_batched(Ws, options: Options | None = None, stream=None, sync: bool = 
     return list(zip(Ds, Ps))
 
 
-def solve(W, options: Options | None = None, stream=None, sync: bool = True):
-    """Out-of-place solve of a CUDA n x n weight matrix: returns (D, P) views."""
+def solve(W, options: Options | None = None, stream=None, sync: bool = True,
+          with_pred: bool = True):
+    """Out-of-place solve of a CUDA n x n weight matrix: returns (D, P) views
+    (P is None when with_pred is False: a distance-only solve)."""
     import torch
     n = W.shape[0]
     ld = padded(n)
     Dbuf = torch.empty((n, ld), dtype=W.dtype, device=W.device)
-    Pbuf = torch.empty((n, ld), dtype=torch.int32, device=W.device)
-    D, P = Dbuf[:, :n], Pbuf[:, :n]
+    D = Dbuf[:, :n]
+    P = None
+    if with_pred:
+        P = torch.empty((n, ld), dtype=torch.int32, device=W.device)[:, :n]
     D.copy_(W)
     fw_solve_ex(D, P, options, stream)
     if sync:

@@ -154,8 +154,9 @@ static fw_status get_ws(cudaStream_t s, size_t need, StreamWs** out) {
   return FW_OK;
 }
 
+// pred may be null: a distance-only solve.
 fw_status check_matrix_args(const void* dist, const void* pred, int64_t n, int64_t ld) {
-  if (!dist || !pred) return FW_ERR_ARG;
+  if (!dist) return FW_ERR_ARG;
   if (n <= 0 || n > 131072 || ld < n || (ld % 4) != 0) return FW_ERR_ARG;
   if ((reinterpret_cast<uintptr_t>(dist) & 15) || (reinterpret_cast<uintptr_t>(pred) & 15))
     return FW_ERR_ARG;
@@ -325,7 +326,7 @@ fw_status fw_sync_status(void* stream) {
 
 fw_status fw_solve_host(void* dist_host, int32_t* pred_host, int64_t n, int64_t ld,
                         fw_dtype dtype, const fw_options* opt, void* stream) {
-  if (!dist_host || !pred_host) return FW_ERR_ARG;
+  if (!dist_host) return FW_ERR_ARG;
   if (n <= 0 || n > 131072 || ld < n || (ld % 4) != 0) return FW_ERR_ARG;
   if (dtype != FW_I32 && dtype != FW_F32) return FW_ERR_ARG;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -353,10 +354,12 @@ fw_status fw_solve_host(void* dist_host, int32_t* pred_host, int64_t n, int64_t 
   }
   if (cudaMemcpyAsync(dd, dist_host, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
     return FW_ERR_CUDA;
-  fw_status st = fw_solve_ex(dd, reinterpret_cast<int32_t*>(dp), n, ld, dtype, opt, stream);
+  fw_status st = fw_solve_ex(dd, pred_host ? reinterpret_cast<int32_t*>(dp) : nullptr, n, ld,
+                             dtype, opt, stream);
   if (st != FW_OK) return st;
   if (cudaMemcpyAsync(dist_host, dd, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-      cudaMemcpyAsync(pred_host, dp, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+      (pred_host &&
+       cudaMemcpyAsync(pred_host, dp, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess))
     return FW_ERR_CUDA;
   return fw_sync_status(stream);
 }

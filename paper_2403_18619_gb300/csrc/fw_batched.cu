@@ -75,6 +75,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_batched_ws(BatchParams<T> p) 
 template <typename T>
 __global__ void __launch_bounds__(256) k_batched_init(const Args<T>* graphs) {
   const Args<T> a = graphs[blockIdx.y];
+  if (!a.P) return;  // distance-only
   const int64_t total = a.n * a.n;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
@@ -88,6 +89,7 @@ __global__ void __launch_bounds__(256) k_batched_init(const Args<T>* graphs) {
 // ViaPred in fw_device.cuh); blockIdx.y is the graph.
 __global__ void __launch_bounds__(256) k_batched_resolve(const Args<int32_t>* graphs) {
   const Args<int32_t> a = graphs[blockIdx.y];
+  if (!a.P) return;  // distance-only
   const int64_t total = a.n * a.n;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
@@ -344,17 +346,17 @@ fw_status solve_plan(fw_batched_plan* p, void* const* dist, int32_t* const* pred
   if (!st) return FW_ERR_NOMEM;
   bool changed = st != p->cur_status;
   for (int64_t g = 0; g < p->batch && !changed; ++g)
-    changed = dist[g] != p->cur_dist[g] || (void*)pred[g] != p->cur_pred[g];
+    changed = dist[g] != p->cur_dist[g] || (void*)(pred ? pred[g] : nullptr) != p->cur_pred[g];
   if (changed) {
     // new buffers: refresh the device tables, then re-record the graph
     if (cudaStreamSynchronize(s) != cudaSuccess) return FW_ERR_CUDA;
     A* ha = reinterpret_cast<A*>(p->h_args.data());
     for (int64_t g = 0; g < p->batch; ++g) {
       ha[g].D = reinterpret_cast<T*>(dist[g]);
-      ha[g].P = pred[g];
+      ha[g].P = pred ? pred[g] : nullptr;
       ha[g].status = st;
       p->cur_dist[g] = dist[g];
-      p->cur_pred[g] = pred[g];
+      p->cur_pred[g] = ha[g].P;
     }
     p->cur_status = st;
     if (cudaMemcpy(p->d_args, p->h_args.data(), p->h_args.size(), cudaMemcpyHostToDevice) !=
@@ -480,10 +482,11 @@ fw_status fw_batched_plan_create(fw_batched_plan** plan, const int64_t* n, const
 
 fw_status fw_solve_batched(fw_batched_plan* p, void* const* dist, int32_t* const* pred,
                            void* stream) {
-  if (!p || !dist || !pred) return FW_ERR_ARG;
+  if (!p || !dist) return FW_ERR_ARG;  // pred null: distance-only for every graph
   for (int64_t g = 0; g < p->batch; ++g) {
-    if (!dist[g] || !pred[g] || dist[g] == (void*)pred[g]) return FW_ERR_ARG;
-    if ((reinterpret_cast<uintptr_t>(dist[g]) & 15) || (reinterpret_cast<uintptr_t>(pred[g]) & 15))
+    int32_t* pg = pred ? pred[g] : nullptr;
+    if (!dist[g] || dist[g] == (void*)pg) return FW_ERR_ARG;
+    if ((reinterpret_cast<uintptr_t>(dist[g]) & 15) || (reinterpret_cast<uintptr_t>(pg) & 15))
       return FW_ERR_ARG;
   }
   int dev = 0;

@@ -510,6 +510,34 @@ __device__ __forceinline__ void core_generic(const T* __restrict__ As, const T* 
   }
 }
 
+// Distance-only relaxation: acc[m][n] = min(acc[m][n], min_kk A + B), two
+// instructions per relaxation (add, min), no argmin.
+template <int BS, typename T, int K>
+__device__ __forceinline__ void core_min(const T* __restrict__ As, const T* __restrict__ Bs,
+                                         T (&acc)[Geo<BS>::TM][Geo<BS>::TM], int tx, int ty) {
+  using Gm = Geo<BS>;
+  constexpr int G = Gm::G, TM = Gm::TM;
+#pragma unroll 2
+  for (int kk = 0; kk < K; ++kk) {
+    T a[TM], b[TM];
+#pragma unroll
+    for (int g = 0; g < Gm::NG; ++g) {
+      T ta[G], tb[G];
+      vload_s<G>(ta, As + kk * BS + g * Gm::SPAN + ty * G);
+      vload_s<G>(tb, Bs + kk * BS + g * Gm::SPAN + tx * G);
+#pragma unroll
+      for (int e = 0; e < G; ++e) { a[g * G + e] = ta[e]; b[g * G + e] = tb[e]; }
+    }
+#pragma unroll
+    for (int m = 0; m < TM; ++m)
+#pragma unroll
+      for (int nn = 0; nn < TM; ++nn) {
+        if constexpr (Num<T>::kInt) acc[m][nn] = min(a[m] + b[nn], acc[m][nn]);
+        else acc[m][nn] = fminf(a[m] + b[nn], acc[m][nn]);
+      }
+  }
+}
+
 // ------------------------------------------------------------- phase 1 ----
 
 // OR of a predicate over the 256 compute threads (one named barrier).
@@ -547,6 +575,7 @@ template <typename T, int BS>
 __device__ __forceinline__ void pivot_store_pred(const Args<T>& a, int r,
                                                  const int32_t (&p)[Geo<BS>::TM][Geo<BS>::TM],
                                                  int tx, int ty) {
+  if (!a.P) return;  // distance-only
   store_tile<BS>(a.P, p, a.n, a.ld, r, r, tx, ty);
   put_tile<BS, false>(a.pivP + (size_t)(r & 1) * BS * BS, p, tx, ty);
 }
@@ -690,79 +719,86 @@ __device__ __forceinline__ void pivot_packed(const Args<T>& a, int r, void* smem
       dst[e] = v == K::CAP ? Num<T>::inf() : (T)v;
     }
   bar_compute();
-  constexpr int kWalk = 8;  // hops walked directly; longer chains fall back to jumping
   int32_t pr[TM][TM];
-  bool unresolved = false;
-  {
-    // all of a thread's chains advance one hop at a time, so that the
-    // dependent shared loads of different chains overlap; c is each chain's
-    // current row (ended when its nxt entry is negative)
-    int c[TM][TM];
+  if (!a.P) {  // distance-only: no predecessors to resolve
 #pragma unroll
     for (int mm = 0; mm < TM; ++mm)
 #pragma unroll
-      for (int nn = 0; nn < TM; ++nn) c[mm][nn] = Gm::idx(ty, mm);
-    bool moved = true;
+      for (int nn = 0; nn < TM; ++nn) pr[mm][nn] = -1;
+  } else {
+    constexpr int kWalk = 8;  // hops walked directly; longer chains fall back to jumping
+    bool unresolved = false;
+    {
+      // all of a thread's chains advance one hop at a time, so that the
+      // dependent shared loads of different chains overlap; c is each chain's
+      // current row (ended when its nxt entry is negative)
+      int c[TM][TM];
+#pragma unroll
+      for (int mm = 0; mm < TM; ++mm)
+#pragma unroll
+        for (int nn = 0; nn < TM; ++nn) c[mm][nn] = Gm::idx(ty, mm);
+      bool moved = true;
 #pragma unroll 1
-    for (int hop = 0; hop < kWalk && moved; ++hop) {
-      moved = false;
+      for (int hop = 0; hop < kWalk && moved; ++hop) {
+        moved = false;
+#pragma unroll
+        for (int mm = 0; mm < TM; ++mm)
+#pragma unroll
+          for (int nn = 0; nn < TM; ++nn) {
+            const int nx = nxt[c[mm][nn] * BS + Gm::idx(tx, nn)];
+            if (nx >= 0) {
+              c[mm][nn] = nx;
+              moved = true;
+            }
+          }
+        moved = __any_sync(0xffffffffu, moved);
+      }
+      // a warp that still moved on its last allowed hop may hold longer chains
+      unresolved = moved;
 #pragma unroll
       for (int mm = 0; mm < TM; ++mm)
 #pragma unroll
-        for (int nn = 0; nn < TM; ++nn) {
-          const int nx = nxt[c[mm][nn] * BS + Gm::idx(tx, nn)];
-          if (nx >= 0) {
-            c[mm][nn] = nx;
-            moved = true;
-          }
-        }
-      moved = __any_sync(0xffffffffu, moved);
+        for (int nn = 0; nn < TM; ++nn) pr[mm][nn] = val[c[mm][nn] * BS + Gm::idx(tx, nn)];
     }
-    // a warp that still moved on its last allowed hop may hold longer chains
-    unresolved = moved;
+    if (bar_compute_or(unresolved)) {
+      // pointer jumping: every round doubles the resolved chain length, and a
+      // chain is at most BS long (its steps strictly decrease)
+      for (int round = 0; (1 << round) <= 2 * BS; ++round) {
+        int nk[TM][TM];
 #pragma unroll
-    for (int mm = 0; mm < TM; ++mm)
+        for (int mm = 0; mm < TM; ++mm)
 #pragma unroll
-      for (int nn = 0; nn < TM; ++nn) pr[mm][nn] = val[c[mm][nn] * BS + Gm::idx(tx, nn)];
-  }
-  if (bar_compute_or(unresolved)) {
-    // pointer jumping: every round doubles the resolved chain length, and a
-    // chain is at most BS long (its steps strictly decrease)
-    for (int round = 0; (1 << round) <= 2 * BS; ++round) {
-      int nk[TM][TM];
+          for (int nn = 0; nn < TM; ++nn) {
+            const int col = Gm::idx(tx, nn);
+            const int k = nxt[Gm::idx(ty, mm) * BS + col];
+            nk[mm][nn] = -2;
+            if (k >= 0) {
+              const int nkk = nxt[k * BS + col];
+              nk[mm][nn] = nkk;
+              if (nkk < 0) pr[mm][nn] = val[k * BS + col];
+            }
+          }
+        bar_compute();
+#pragma unroll
+        for (int mm = 0; mm < TM; ++mm)
+#pragma unroll
+          for (int nn = 0; nn < TM; ++nn) {
+            if (nk[mm][nn] == -2) continue;
+            const int e = Gm::idx(ty, mm) * BS + Gm::idx(tx, nn);
+            if (nk[mm][nn] < 0) {
+              val[e] = pr[mm][nn];
+              nxt[e] = -1;
+            } else {
+              nxt[e] = nk[mm][nn];
+            }
+          }
+        bar_compute();
+      }
 #pragma unroll
       for (int mm = 0; mm < TM; ++mm)
 #pragma unroll
-        for (int nn = 0; nn < TM; ++nn) {
-          const int col = Gm::idx(tx, nn);
-          const int k = nxt[Gm::idx(ty, mm) * BS + col];
-          nk[mm][nn] = -2;
-          if (k >= 0) {
-            const int nkk = nxt[k * BS + col];
-            nk[mm][nn] = nkk;
-            if (nkk < 0) pr[mm][nn] = val[k * BS + col];
-          }
-        }
-      bar_compute();
-#pragma unroll
-      for (int mm = 0; mm < TM; ++mm)
-#pragma unroll
-        for (int nn = 0; nn < TM; ++nn) {
-          if (nk[mm][nn] == -2) continue;
-          const int e = Gm::idx(ty, mm) * BS + Gm::idx(tx, nn);
-          if (nk[mm][nn] < 0) {
-            val[e] = pr[mm][nn];
-            nxt[e] = -1;
-          } else {
-            nxt[e] = nk[mm][nn];
-          }
-        }
-      bar_compute();
+        for (int nn = 0; nn < TM; ++nn) pr[mm][nn] = val[Gm::idx(ty, mm) * BS + Gm::idx(tx, nn)];
     }
-#pragma unroll
-    for (int mm = 0; mm < TM; ++mm)
-#pragma unroll
-      for (int nn = 0; nn < TM; ++nn) pr[mm][nn] = val[Gm::idx(ty, mm) * BS + Gm::idx(tx, nn)];
   }
   stamp(3);
   {
@@ -785,7 +821,14 @@ __device__ __noinline__ void pivot_eager(const Args<T>& a, int r, void* smem_raw
   T d[TM][TM];
   int32_t p[TM][TM];
   load_tile<BS>(d, a.D, a.n, a.ld, r, r, tx, ty, Num<T>::inf());
-  load_tile<BS>(p, a.P, a.n, a.ld, r, r, tx, ty, (int32_t)-1);
+  if (a.P) {
+    load_tile<BS>(p, a.P, a.n, a.ld, r, r, tx, ty, (int32_t)-1);
+  } else {
+#pragma unroll
+    for (int mm = 0; mm < TM; ++mm)
+#pragma unroll
+      for (int nn = 0; nn < TM; ++nn) p[mm][nn] = -1;
+  }
   stamp(1);
   T* rowD = reinterpret_cast<T*>(smem_raw);  // [2][BS]
   int32_t* rowP = reinterpret_cast<int32_t*>(rowD + 2 * BS);
@@ -863,7 +906,14 @@ __device__ __noinline__ void task_pivot(const Args<T>& a, int r, void* smem_raw,
     T d[TM][TM];
     int32_t p[TM][TM];
     load_tile<BS>(d, a.D, a.n, a.ld, r, r, tx, ty, Num<T>::inf());
-    load_tile<BS>(p, a.P, a.n, a.ld, r, r, tx, ty, (int32_t)-1);
+    if (a.P) {
+      load_tile<BS>(p, a.P, a.n, a.ld, r, r, tx, ty, (int32_t)-1);
+    } else {
+#pragma unroll
+      for (int mm = 0; mm < TM; ++mm)
+#pragma unroll
+        for (int nn = 0; nn < TM; ++nn) p[mm][nn] = -1;
+    }
     int bnd = 0, dummy = 0;
 #pragma unroll
     for (int mm = 0; mm < TM; ++mm)
@@ -968,7 +1018,9 @@ __device__ __forceinline__ int panel_store_group(const Args<T>& a, int r, int t,
       if (gi < a.n) {
         if (gj0 + G <= a.n) {
           vstore<G>(a.D + gi * a.ld + gj0, vs);
-          if constexpr (is_row) {
+          if (!a.P) {
+            // distance-only
+          } else if constexpr (is_row) {
             vstore<G>(a.P + gi * a.ld + gj0, vp);
           } else {
 #pragma unroll
@@ -980,14 +1032,16 @@ __device__ __forceinline__ int panel_store_group(const Args<T>& a, int r, int t,
           for (int q = 0; q < G; ++q)
             if (gj0 + q < a.n) {
               a.D[gi * a.ld + gj0 + q] = vs[q];
-              if (is_row || imp[e][gg * G + q]) a.P[gi * a.ld + gj0 + q] = vp[q];
+              if (a.P && (is_row || imp[e][gg * G + q])) a.P[gi * a.ld + gj0 + q] = vp[q];
             }
         }
       }
       if constexpr (is_row) {
         // B-form snapshots: raw, pred and packed key (code bits zero)
         vstore<G>(a.rowR + tile_off + lr * BS + lc0, vs);
-        if constexpr (!ViaPred<T>::kOn) vstore<G>(a.rowP + tile_off + lr * BS + lc0, vp);
+        if constexpr (!ViaPred<T>::kOn) {
+          if (a.P) vstore<G>(a.rowP + tile_off + lr * BS + lc0, vp);
+        }
         if constexpr (Num<T>::kInt) {
           uint32_t kq[G];
 #pragma unroll
@@ -1072,7 +1126,7 @@ __device__ __noinline__ int panel_packed(const Args<T>& a, int r, int t,
         const int32_t v = (int32_t)(acc[m][nn] >> K::KB);
         sv[e][nn] = v == K::CAP ? Num<T>::inf() : (T)v;
         imp[e][nn] = c != 0;
-        np[e][nn] = c ? Ps[(c - 1) * BS + lc] : (is_row ? Ps[Gm::idx(ty, m) * BS + lc] : -1);
+        np[e][nn] = !a.P ? -1 : c ? Ps[(c - 1) * BS + lc] : (is_row ? Ps[Gm::idx(ty, m) * BS + lc] : -1);
       }
     }
     nb = max(nb, panel_store_group<T, BS, is_row>(a, r, t, g, sv, np, imp, tx, ty));
@@ -1132,7 +1186,7 @@ __device__ __noinline__ int panel_eager(const Args<T>& a, int r, int t, const T*
         const int c = code[m][nn];
         sv[e][nn] = s[m][nn];
         imp[e][nn] = c != 0;
-        np[e][nn] = c ? Ps[(c - 1) * BS + lc] : (is_row ? Ps[Gm::idx(ty, m) * BS + lc] : -1);
+        np[e][nn] = !a.P ? -1 : c ? Ps[(c - 1) * BS + lc] : (is_row ? Ps[Gm::idx(ty, m) * BS + lc] : -1);
       }
     }
     nb = max(nb, panel_store_group<T, BS, is_row>(a, r, t, g, sv, np, imp, tx, ty));
@@ -1167,10 +1221,13 @@ __device__ __noinline__ void task_panel(const Args<T>& a, int r, int t, bool is_
   stamp(0);
 
   // predecessor source, staged (its loads overlap the operand loads below)
-  if (is_row)
+  if (!a.P) {
+    // distance-only: no predecessor source
+  } else if (is_row) {
     stage_tile_i32<BS>(Ps, a.P, a.n, a.ld, ti, tj, nullptr);
-  else
+  } else {
     stage_tile_i32<BS>(Ps, nullptr, 0, 0, 0, 0, a.pivP + (size_t)slot * BS * BS);
+  }
 
   bool fast = false;
   {
@@ -1316,7 +1373,7 @@ __device__ void task_minplus(const Args<T>& a, int r, int ti, int tj, void* smem
         if (c && gi < a.n && gj < a.n) {
           const int32_t nv = (int32_t)(acc[m][nn] >> K::KB);
           a.D[gi * a.ld + gj] = (T)nv;
-          a.P[gi * a.ld + gj] = ViaPred<T>::kOn
+          if (a.P) a.P[gi * a.ld + gj] = ViaPred<T>::kOn
                                     ? via_code((int64_t)r * BS + c - 1)
                                     : __ldcg(rowP + (c - 1) * BS + Gm::idx(tx, nn));
           if (gi == gj && nv < 0) neg = true;
@@ -1339,7 +1396,7 @@ __device__ void task_minplus(const Args<T>& a, int r, int ti, int tj, void* smem
         const int64_t gj = (int64_t)tj * BS + Gm::idx(tx, nn);
         if (arg[m][nn] && gi < a.n && gj < a.n) {
           a.D[gi * a.ld + gj] = old[m][nn];
-          a.P[gi * a.ld + gj] = ViaPred<T>::kOn
+          if (a.P) a.P[gi * a.ld + gj] = ViaPred<T>::kOn
                                     ? via_code((int64_t)r * BS + arg[m][nn] - 1)
                                     : __ldcg(rowP + (arg[m][nn] - 1) * BS + Gm::idx(tx, nn));
           if (gi == gj && old[m][nn] < T(0)) neg = true;

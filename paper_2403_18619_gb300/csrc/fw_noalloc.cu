@@ -76,8 +76,10 @@ cudaError_t run(T* D, int32_t* P, int64_t n, int64_t ld, unsigned char* base, in
 
   int64_t blocks = (n * n + 255) / 256;
   if (blocks > (int64_t)sms * 8) blocks = (int64_t)sms * 8;
-  k_init_pred<T><<<(int)blocks, 256, 0, s>>>(D, P, n, ld);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (P) {
+    k_init_pred<T><<<(int)blocks, 256, 0, s>>>(D, P, n, ld);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
 
   const size_t smem = WsLayout<BS, T>::bytes();
   auto kern = k_persistent_ws<T, BS>;
@@ -105,7 +107,7 @@ cudaError_t run(T* D, int32_t* P, int64_t n, int64_t ld, unsigned char* base, in
   // this entry point keeps the per-row tile copies
   CUtensorMap tm{};
   if ((e = cudaLaunchKernelEx(&lc, kern, a, tm, 0)) != cudaSuccess) return e;
-  if constexpr (ViaPred<T>::kOn) {
+  if (ViaPred<T>::kOn && P) {
     k_resolve_pred<<<(int)blocks, 256, 0, s>>>(P, n, ld);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
@@ -116,7 +118,7 @@ cudaError_t run(T* D, int32_t* P, int64_t n, int64_t ld, unsigned char* base, in
 
 extern "C" fw_status fw_solve_noalloc(void* dist, int32_t* pred, int64_t n, int64_t ld,
                                       fw_dtype dtype, void* stream) {
-  if (!dist || !pred || dist == (void*)pred) return FW_ERR_ARG;
+  if (!dist || dist == (void*)pred) return FW_ERR_ARG;  // pred null: distance-only
   if (n <= 0 || ld < n || (ld % 4) != 0) return FW_ERR_ARG;
   if ((reinterpret_cast<uintptr_t>(dist) & 15) || (reinterpret_cast<uintptr_t>(pred) & 15))
     return FW_ERR_ARG;

@@ -40,10 +40,12 @@ __global__ void __launch_bounds__(kProbeThreads, 1)
       for (int m = 0; m < 8; ++m)
 #pragma unroll
         for (int n = 0; n < 8; ++n) {
+          // a different column operand in each of the 4 unrolled steps: with
+          // the same one, min(x, min(x, acc)) would fold to a single min
           if constexpr (kInt) {
-            acc[m][n] = __viaddmin_u32(a[m], b[n], acc[m][n]);
+            acc[m][n] = __viaddmin_u32(a[m], b[(n + u) & 7], acc[m][n]);
           } else {
-            float x = __uint_as_float(a[m]) + __uint_as_float(b[n]);
+            float x = __uint_as_float(a[m]) + __uint_as_float(b[(n + u) & 7]);
             acc[m][n] = __float_as_uint(fminf(x, __uint_as_float(acc[m][n])));
           }
         }

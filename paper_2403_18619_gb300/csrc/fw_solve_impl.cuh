@@ -60,7 +60,7 @@ cudaError_t launch_bs(T* D, int32_t* P, int64_t n, int64_t ld, const fwh::SolveW
   const size_t smem = Smem<BS>::bytes();
   cudaError_t e;
 
-  {
+  if (P) {  // null: distance-only
     int64_t blocks = (n * n + 255) / 256;
     const int cap = fwh::num_sms() * 8;
     if (blocks > cap) blocks = cap;
@@ -115,7 +115,7 @@ cudaError_t launch_bs(T* D, int32_t* P, int64_t n, int64_t ld, const fwh::SolveW
     if ((e = cudaLaunchKernelEx(&lc, kern, a, tm, use_tmap)) != cudaSuccess) return e;
   }
   if (cfg.ev_stop) cudaEventRecord(cfg.ev_stop, s);
-  if constexpr (ViaPred<T>::kOn) {
+  if (ViaPred<T>::kOn && P) {
     int64_t blocks = (n * n + 255) / 256;
     const int cap = fwh::num_sms() * 8;
     if (blocks > cap) blocks = cap;

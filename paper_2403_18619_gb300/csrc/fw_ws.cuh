@@ -113,12 +113,98 @@ struct PipeCnt {
 
 // ------------------------------------------------------------ compute side ----
 
+// Distance-only remaining-tile task (no predecessors, generic kernel): add +
+// min over the streamed chunks, then the whole tile written back (unchanged
+// entries rewrite their own value).  A function of its own, so that the
+// packed kernel's register allocation does not see it.
+template <typename T, int BS, int LBS>
+__device__ __noinline__ bool ws_minplus_dist(TileCtx<T> c, int ti, int tj, unsigned char* smem,
+                                             WsBars* wb, PipeCnt& pc, uint64_t* tr) {
+  using Gm = Geo<BS>;
+  using L = WsLayout<LBS, T>;
+  using C = WsChunk<BS, T>;
+  constexpr int TM = Gm::TM, G = Gm::G;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4, lane = tid & 31;
+  const T* Dbuf = reinterpret_cast<const T*>(smem + L::d_off());
+  unsigned char* ring = smem + L::ring_off();
+  const int64_t row0 = (int64_t)ti * BS, col0 = (int64_t)tj * BS;
+  const int nrow = (int)(c.n - row0 < BS ? c.n - row0 : BS);
+  const int ncol = (int)(c.n - col0 < BS ? c.n - col0 : BS);
+  const bool full = nrow == BS && ncol == BS;
+  const long long t_a = tr ? clock64() : 0;
+  long long cw = 0;
+  if (!mbar_wait(&wb->d_full, pc.d & 1, c.status, c.abort_flag, c.timeout_ns)) return false;
+  const long long t_b = tr ? clock64() : 0;
+  T acc[TM][TM];
+#pragma unroll
+  for (int m = 0; m < TM; ++m) {
+    const int lr = Gm::idx(ty, m);
+#pragma unroll
+    for (int g = 0; g < Gm::NG; ++g) {
+      const int lc0 = g * Gm::SPAN + tx * G;
+      T tmp[G];
+      vload_s<G>(tmp, Dbuf + lr * BS + lc0);
+#pragma unroll
+      for (int e = 0; e < G; ++e)
+        acc[m][g * G + e] = (lr < nrow && lc0 + e < ncol) ? tmp[e] : Num<T>::inf();
+    }
+  }
+  __syncwarp();
+  if (lane == 0) mbar_arrive(&wb->d_empty);
+  ++pc.d;
+  for (int ch = 0; ch < C::NC; ++ch) {
+    const unsigned st = pc.chunk & 1;
+    const long long w0 = tr ? clock64() : 0;
+    if (!mbar_wait(&wb->chunk_full[st], (pc.chunk >> 1) & 1, c.status, c.abort_flag,
+                   c.timeout_ns))
+      return false;
+    if (tr) cw += clock64() - w0;
+    const T* As = reinterpret_cast<const T*>(ring + st * L::kStage);
+    const T* Bs = As + C::CK * BS;
+    core_min<BS, T, C::CK>(As, Bs, acc, tx, ty);
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&wb->chunk_empty[st]);
+    ++pc.chunk;
+  }
+  if (tr) {
+    tr[7] = cyc20(t_b - t_a) | (cyc20(cw) << 20);
+    tr[8] = (uint64_t)(clock64() - t_a);
+  }
+  T* Drow = c.D + row0 * c.ld + col0;
+  bool neg = false;
+#pragma unroll
+  for (int m = 0; m < TM; ++m) {
+    const int lr = Gm::idx(ty, m);
+#pragma unroll
+    for (int g = 0; g < Gm::NG; ++g) {
+      const int lc0 = g * Gm::SPAN + tx * G;
+      T v[G];
+#pragma unroll
+      for (int e = 0; e < G; ++e) {
+        v[e] = acc[m][g * G + e];
+        neg |= (row0 + lr == col0 + lc0 + e) && v[e] < T(0);
+      }
+      if (full) {
+        vstore<G>(Drow + lr * c.ld + lc0, v);
+      } else if (lr < nrow) {
+#pragma unroll
+        for (int e = 0; e < G; ++e)
+          if (lc0 + e < ncol) Drow[lr * c.ld + lc0 + e] = v[e];
+      }
+    }
+  }
+  if (tr) tr[8] |= (uint64_t)(clock64() - t_a) << 32;
+  if (neg) atomicOr(c.status, kStNegCycle);
+  return true;
+}
+
 // Remaining-tile task (phase 4 of round r, tile ti,tj).  Returns false if an
 // operand never arrived (the kernel then stops).
 template <typename T, int BS, int LBS>
 __device__ __forceinline__ bool ws_minplus(TileCtx<T> c, int ti, int tj, bool fast,
                                         unsigned char* smem, WsBars* wb, PipeCnt& pc,
                                         uint64_t* tr) {
+  if (!fast && !c.P) return ws_minplus_dist<T, BS, LBS>(c, ti, tj, smem, wb, pc, tr);
   using Gm = Geo<BS>;
   using K = Keys<BS>;
   using L = WsLayout<LBS, T>;
@@ -221,9 +307,12 @@ __device__ __forceinline__ bool ws_minplus(TileCtx<T> c, int ti, int tj, bool fa
             }
             if (cg) vstore<G>(Drow + lr * c.ld + lc0, dv);
 #pragma unroll
-            for (int e = 0; e < G; ++e) {
-              const int code = (int)(acc[m][g * G + e] & K::MASK);
-              if (code) Prow[lr * c.ld + lc0 + e] = via0 - code;
+            if (c.P) {
+#pragma unroll
+              for (int e = 0; e < G; ++e) {
+                const int code = (int)(acc[m][g * G + e] & K::MASK);
+                if (code) Prow[lr * c.ld + lc0 + e] = via0 - code;
+              }
             }
           }
         }
@@ -239,7 +328,7 @@ __device__ __forceinline__ bool ws_minplus(TileCtx<T> c, int ti, int tj, bool fa
             const int lc = Gm::idx(tx, nn);
             if (code && lr < nrow && lc < ncol) {
               Drow[lr * c.ld + lc] = (T)(int32_t)(acc[m][nn] >> K::KB);
-              Prow[lr * c.ld + lc] = via0 - code;
+              if (c.P) Prow[lr * c.ld + lc] = via0 - code;
             }
           }
         }
@@ -267,6 +356,7 @@ __device__ __forceinline__ bool ws_minplus(TileCtx<T> c, int ti, int tj, bool fa
     }
     const long long t_c = tr ? clock64() : 0;
     if constexpr (!ViaPred<T>::kOn) {
+      // (this branch always has predecessors)
       if (!mbar_wait(&wb->p_full, pc.p & 1, c.status, c.abort_flag, c.timeout_ns)) return false;
     }
     if (tr) {
@@ -291,9 +381,11 @@ __device__ __forceinline__ bool ws_minplus(TileCtx<T> c, int ti, int tj, bool fa
   }
   if (tr) tr[8] |= (uint64_t)(clock64() - t_a) << 32;  // whole task
   if constexpr (!ViaPred<T>::kOn) {
-    __syncwarp();
-    if (lane == 0) mbar_arrive(&wb->p_empty);
-    ++pc.p;
+    if (c.P) {
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&wb->p_empty);
+      ++pc.p;
+    }
   }
   if (neg) atomicOr(c.status, kStNegCycle);
   return true;
@@ -477,7 +569,7 @@ __device__ void issue_operands(const Args<T>& a, const fwh::Task& k, bool fast, 
     ++pc.chunk;
   }
   // predecessor tile of the row panel snapshot (fp32; int32 records "via" codes)
-  if constexpr (!ViaPred<T>::kOn) {
+  if (!ViaPred<T>::kOn && a.P) {
     if (lane == 0) {
       mbar_wait(&wb->p_empty, (pc.p & 1) ^ 1, a.status, a.abort_flag, a.timeout_ns);
       mbar_expect_tx(&wb->p_full, (unsigned)C::kTile);

@@ -101,3 +101,37 @@ def check_f32(W, D, P, Do, Po, rows=None):
     safe = reach & (mg > 2 * tol) & (hops > 0)
     assert (Pg[safe] == Po[safe]).all(), "fp32 pred differs on margin-safe pairs"
     return int(safe.sum())
+
+
+def check_f32_dist(W, D, Do, Po):
+    """fp32 distances only (a distance-only solve): within 1e-6 * hops relative
+    of the fp64 oracle, reachability exact."""
+    reach = np.isfinite(Do)
+    assert (np.isfinite(D) == reach).all(), "reachability differs"
+    hops = oracle.hops(Po)
+    tol = 1e-6 * np.maximum(hops, 1) * np.abs(Do)
+    err = np.abs(D.astype(np.float64) - Do)
+    err[~reach] = 0
+    worst = np.unravel_index(np.argmax(err - tol), err.shape)
+    assert (err <= tol).all(), "fp32 error %g > tol %g at %s" % (err[worst], tol[worst], worst)
+
+
+def gpu_solve_dist_only(W: np.ndarray, *, bs=0, driver=0, packed=1, extra_ld=0):
+    """Distance-only solve (pred = NULL) through the C ABI; returns host D and
+    checks that the padding columns were left alone."""
+    import torch
+    m = fw()
+    n = W.shape[0]
+    ld = m.padded(n) + extra_ld
+    tdt = torch.int32 if W.dtype == np.int32 else torch.float32
+    canary = CANARY_I if W.dtype == np.int32 else CANARY_F
+    Dbuf = torch.full((n, ld), float(canary) if tdt == torch.float32 else int(canary),
+                      dtype=tdt, device="cuda")
+    D = Dbuf[:, :n]
+    D.copy_(torch.from_numpy(np.ascontiguousarray(W)))
+    m.fw_solve_ex(D, None, m.Options.default(bs=bs, driver=driver, packed_keys=packed))
+    m.fw_sync_status()
+    Dh = Dbuf.cpu().numpy()
+    if ld > n:
+        assert (Dh[:, n:] == canary).all(), "dist padding was written"
+    return Dh[:, :n].copy()

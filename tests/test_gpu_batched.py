@@ -5,12 +5,12 @@ import pytest
 
 import graphgen
 import oracle
-from fwtest import INF, check_f32, check_int_full, fw
+from fwtest import INF, check_f32, check_f32_dist, check_int_full, fw
 
 pytestmark = pytest.mark.gpu
 
 
-def _run(Ws, options=None, reps=1):
+def _run(Ws, options=None, reps=1, with_pred=True):
     import torch
     m = fw()
     Ds, Ps, ns, lds = [], [], [], []
@@ -28,7 +28,8 @@ def _run(Ws, options=None, reps=1):
     for _ in range(reps):
         for W, Db in zip(Ws, Ds):
             Db[:, :W.shape[0]].copy_(torch.from_numpy(W))
-        plan.solve([D[:, :n] for D, n in zip(Ds, ns)], [P[:, :n] for P, n in zip(Ps, ns)])
+        plan.solve([D[:, :n] for D, n in zip(Ds, ns)],
+                   [P[:, :n] for P, n in zip(Ps, ns)] if with_pred else None)
         m.fw_sync_status()
     bs, tasks = plan.info()
     plan.close()
@@ -111,3 +112,20 @@ def test_bs_table_and_autotune():
     assert (ms[:2] > 0).all()
     assert (m.fw_bs_table() == table).all()
     m.fw_bs_table(old)
+
+
+def test_batched_distance_only():
+    """preds = NULL: every graph solved for distances only (int32 exact, fp32
+    within tolerance); the predecessor buffers are never written."""
+    Ws = _int_batch(21, 20, 1, 400)
+    out, _, _ = _run(Ws, with_pred=False)
+    for W, (D, P) in zip(Ws, out):
+        Do, _ = oracle.fw_i64(W)
+        np.testing.assert_array_equal(D.astype(np.int64), Do)
+        assert (P == -9).all(), "pred written by a distance-only solve"
+    ns = graphgen.batch_sizes(22, 8, 1, 300)
+    Wf = [graphgen.dense_graph_f32(int(n), seed=2200 + b, p=0.3) for b, n in enumerate(ns)]
+    out, _, _ = _run(Wf, with_pred=False)
+    for W, (D, P) in zip(Wf, out):
+        Do, Po = oracle.fw_f64(W)
+        check_f32_dist(W, D, Do, Po)

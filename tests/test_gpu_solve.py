@@ -10,7 +10,8 @@ import pytest
 
 import graphgen
 import oracle
-from fwtest import (INF, check_f32, check_int_full, check_int_rows, fw, gpu_solve, int_case)
+from fwtest import (INF, check_f32, check_f32_dist, check_int_full, check_int_rows, fw,
+                    gpu_solve, gpu_solve_dist_only, int_case)
 
 pytestmark = pytest.mark.gpu
 
@@ -238,3 +239,45 @@ def test_device_generator_matches_host():
     gdev.fill_f32(f[:, :n], seed=6, p=0.5, kind=1)
     np.testing.assert_array_equal(f[:, :n].cpu().numpy(),
                                   graphgen.dense_graph_f32(n, 6, 0.5, kind=1))
+
+
+# --------------------------------------------------------- distance only ---
+
+@pytest.mark.parametrize("driver", [PERSISTENT, PHASED])
+@pytest.mark.parametrize("n,bs,extra_ld", [(1, 32, 0), (33, 32, 4), (257, 128, 0), (600, 64, 8)])
+def test_distance_only(n, bs, extra_ld, driver):
+    """pred = NULL: the same distances (int32 bit-exact, fp32 within the
+    tolerance), no predecessor work, padding untouched."""
+    W, Do, Po, cnt = int_case(n, 300 + n, 0.4, 1, 60)
+    D = gpu_solve_dist_only(W, bs=bs, driver=driver, extra_ld=extra_ld)
+    np.testing.assert_array_equal(D.astype(np.int64), Do)
+    Wf = graphgen.dense_graph_f32(n, seed=n + 11, p=0.4)
+    Dfo, Pfo = oracle.fw_f64(Wf)
+    Df = gpu_solve_dist_only(Wf, bs=bs, driver=driver, extra_ld=extra_ld)
+    check_f32_dist(Wf, Df, Dfo, Pfo)
+
+
+@pytest.mark.parametrize("packed", [0, 1])
+def test_distance_only_generic_and_large_weights(packed):
+    """Distance-only through the generic int32 kernels: large weights (beyond
+    the packed-key bound) and the packed path switched off."""
+    n = 300
+    W = graphgen.dense_graph_i32(n, seed=41, p=0.3, lo=1 << 18, hi=1 << 19)
+    Do, _ = oracle.fw_i64(W)
+    D = gpu_solve_dist_only(W, bs=64, packed=packed)
+    np.testing.assert_array_equal(D.astype(np.int64), Do)
+
+
+def test_distance_only_host_and_noalloc():
+    import torch
+    m = fw()
+    W, Do, Po, cnt = int_case(200, 9, 0.5, 1, 30)
+    ld = m.padded(200)
+    Dh = np.zeros((200, ld), np.int32)
+    Dh[:, :200] = W
+    m.fw_solve_host(Dh[:, :200], None)
+    np.testing.assert_array_equal(Dh[:, :200].astype(np.int64), Do)
+    D = torch.from_numpy(Dh.copy()).cuda()
+    D[:, :200].copy_(torch.from_numpy(W))
+    m.fw_solve_noalloc(D[:, :200], None)
+    np.testing.assert_array_equal(D[:, :200].cpu().numpy().astype(np.int64), Do)
