@@ -101,6 +101,30 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const void* tmap, int x, 
       "l"(tmap), "r"(x), "r"(y), "r"(smem_u32(bar))
       : "memory");
 }
+// Bulk stores shared -> global through the TMA unit (bulk-group completion:
+// the issuing thread commits and waits for its own groups).  Addresses
+// 16-byte aligned, sizes multiples of 16 bytes.
+__device__ __forceinline__ void bulk_s2g(void* dst, const void* src, unsigned bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst),
+               "r"(smem_u32(src)), "r"(bytes)
+               : "memory");
+}
+// 2-D tiled tensor store (box at element coordinates x = column, y = row;
+// elements outside the tensor are not written).
+__device__ __forceinline__ void tma_store_2d(const void* tmap, int x, int y, const void* src) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group [%0, {%1, %2}], [%3];" ::
+                   "l"(tmap),
+               "r"(x), "r"(y), "r"(smem_u32(src))
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit_wait_all() {
+  asm volatile("cp.async.bulk.commit_group;\n cp.async.bulk.wait_group 0;" ::: "memory");
+}
+// Order this thread's earlier generic shared-memory accesses before its
+// following async-proxy (TMA) accesses.
+__device__ __forceinline__ void fence_proxy_async_shared() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
 // 1-D bulk copy global -> shared through the TMA unit, completing on `bar`.
 // dst, src 16-byte aligned; bytes a multiple of 16.
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes,
@@ -279,6 +303,7 @@ struct Args {
   // 2-D tensor map of D (CUtensorMap, BS x BS boxes) for the persistent
   // driver's tile loads; null: the tile is copied row by row
   const void* tmapD;
+  const void* tmapP;
   // optional per-task trace (persistent driver)
   uint64_t* trace;
   int trace_cap;
@@ -801,15 +826,54 @@ __device__ __forceinline__ void pivot_packed(const Args<T>& a, int r, void* smem
     }
   }
   stamp(3);
-  {
+  // Results out: distances are staged in dst, predecessors go to the nxt
+  // region (free once the walk is done); full tiles and the snapshots leave by
+  // TMA bulk stores, which do not queue behind one another in the SM's
+  // load/store unit the way 64 vector stores per thread do.
+  int32_t* pst = nxt;
+  bar_compute();
+  bool neg = false;
+#pragma unroll
+  for (int mm = 0; mm < TM; ++mm)
+#pragma unroll
+    for (int nn = 0; nn < TM; ++nn) {
+      const int e = Gm::idx(ty, mm) * BS + Gm::idx(tx, nn);
+      if (a.P) pst[e] = pr[mm][nn];
+      if (Gm::idx(ty, mm) == Gm::idx(tx, nn) && dst[e] < T(0)) neg = true;
+    }
+  if (neg) atomicOr(a.status, kStNegCycle);
+  bar_compute();
+  const int64_t r0 = (int64_t)r * BS;
+  // Bulk stores of the live tiles only when the pivot tile lies inside the
+  // matrix: a tensor store clips at 16-byte granules of a row, so a ragged
+  // edge would overwrite the caller's padding columns.
+  const bool whole = r0 + BS <= a.n;
+  if (tid < 32) {
+    fence_proxy_async_shared();
+    const size_t slot = (size_t)(r & 1) * BS * BS;
+    if (tid == 0) {
+      bulk_s2g(a.piv + slot, dst, (unsigned)(BS * BS * sizeof(T)));
+      if (a.P) bulk_s2g(a.pivP + slot, pst, (unsigned)(BS * BS * 4));
+      if (whole && a.tmapD) tma_store_2d(a.tmapD, (int)r0, (int)r0, dst);
+      if (whole && a.P && a.tmapP) tma_store_2d(a.tmapP, (int)r0, (int)r0, pst);
+    }
+    if (whole && !a.tmapD)
+      for (int rr = tid; rr < BS; rr += 32)
+        bulk_s2g(a.D + (r0 + rr) * a.ld + r0, dst + rr * BS, (unsigned)(BS * sizeof(T)));
+    if (whole && a.P && !a.tmapP)
+      for (int rr = tid; rr < BS; rr += 32)
+        bulk_s2g(a.P + (r0 + rr) * a.ld + r0, pst + rr * BS, (unsigned)(BS * 4));
+    bulk_commit_wait_all();
+  }
+  if (!whole) {  // ragged pivot tile: in-range stores
     T dd[TM][TM];
 #pragma unroll
     for (int mm = 0; mm < TM; ++mm)
 #pragma unroll
       for (int nn = 0; nn < TM; ++nn) dd[mm][nn] = dst[Gm::idx(ty, mm) * BS + Gm::idx(tx, nn)];
-    pivot_store_dist<T, BS>(a, r, dd, tx, ty);
+    store_tile<BS>(a.D, dd, a.n, a.ld, r, r, tx, ty);
+    if (a.P) store_tile<BS>(a.P, pr, a.n, a.ld, r, r, tx, ty);
   }
-  pivot_store_pred<T, BS>(a, r, pr, tx, ty);
 }
 
 // Eager pivot: compare and select per relaxation (fp32, large int32 entries).

@@ -106,7 +106,7 @@ cudaError_t run(T* D, int32_t* P, int64_t n, int64_t ld, unsigned char* base, in
   // the tensor map would be a second copy of the caller's layout per call;
   // this entry point keeps the per-row tile copies
   CUtensorMap tm{};
-  if ((e = cudaLaunchKernelEx(&lc, kern, a, tm, 0)) != cudaSuccess) return e;
+  if ((e = cudaLaunchKernelEx(&lc, kern, a, tm, tm, 0)) != cudaSuccess) return e;
   if (ViaPred<T>::kOn && P) {
     k_resolve_pred<<<(int)blocks, 256, 0, s>>>(P, n, ld);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;

@@ -109,10 +109,13 @@ cudaError_t launch_bs(T* D, int32_t* P, int64_t n, int64_t ld, const fwh::SolveW
     attr[0].val.cooperative = 1;
     lc.attrs = attr;
     lc.numAttrs = 1;
-    CUtensorMap tm{};
-    const int use_tmap =
-        fwh::encode_tile_map(&tm, D, n, ld, BS, !Num<T>::kInt) && cfg.tile_tma ? 1 : 0;
-    if ((e = cudaLaunchKernelEx(&lc, kern, a, tm, use_tmap)) != cudaSuccess) return e;
+    CUtensorMap tmD{}, tmP{};
+    int use_tmap = 0;
+    if (cfg.tile_tma) {
+      if (fwh::encode_tile_map(&tmD, D, n, ld, BS, !Num<T>::kInt)) use_tmap |= 1;
+      if (P && fwh::encode_tile_map(&tmP, P, n, ld, BS, false)) use_tmap |= 2;
+    }
+    if ((e = cudaLaunchKernelEx(&lc, kern, a, tmD, tmP, use_tmap)) != cudaSuccess) return e;
   }
   if (cfg.ev_stop) cudaEventRecord(cfg.ev_stop, s);
   if (ViaPred<T>::kOn && P) {

@@ -799,11 +799,12 @@ struct SingleSrc {
   int skip_task;
   uint64_t* trace;
   int trace_cap, trace_stride;
-  __device__ SingleSrc(const Args<T>& x, const void* tmapD)
+  __device__ SingleSrc(const Args<T>& x, const void* tmapD, const void* tmapP)
       : a(x), next(x.ctr), status(x.status), abort_flag(x.abort_flag), timeout_ns(x.timeout_ns),
         skip_task(x.skip_task), trace(x.trace), trace_cap(x.trace_cap),
         trace_stride(x.trace_stride) {
     a.tmapD = tmapD;
+    a.tmapP = tmapP;
   }
   __device__ int64_t total() const { return a.stage_off[a.R + 1]; }
   __device__ fwh::Task resolve(int64_t t, int& g) const {
@@ -816,11 +817,13 @@ struct SingleSrc {
 
 template <typename T, int BS>
 __global__ void __launch_bounds__(kWsThreads, 1)
-    k_persistent_ws(Args<T> a, const __grid_constant__ CUtensorMap tmD, int use_tmap) {
+    k_persistent_ws(Args<T> a, const __grid_constant__ CUtensorMap tmD,
+                    const __grid_constant__ CUtensorMap tmP, int use_tmap) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ WsBars wb;
   __shared__ CtaScratch cs;
-  const SingleSrc<T, BS> src(a, use_tmap ? &tmD : nullptr);
+  // use_tmap: bit 0 the D map, bit 1 the P map
+  const SingleSrc<T, BS> src(a, (use_tmap & 1) ? &tmD : nullptr, (use_tmap & 2) ? &tmP : nullptr);
   ws_engine<T, BS, BS>(src, smem, wb, cs);
 }
 
