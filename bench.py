@@ -38,6 +38,10 @@ P_EDGE = 0.9
 LO, HI = 1, 10_000
 BS = 128
 SAMPLE_N = 2048          # CPU baseline: leading 2048-vertex induced subgraph
+# DRAM bytes (read + write) of one k_persistent_ws launch, from one ncu
+# capture of this workload (profiles/k_persistent_ws_int32_n32768_launches.md);
+# algorithmic: 8 n^3 / BS = 2.20e12 B.  Other configurations: not captured.
+TRAFFIC_BYTES = {(32768, 128, 1): 1.53e12 + 0.66292e12}
 
 
 def workload_name(n=N_FULL):
@@ -439,9 +443,11 @@ def run_gpu(args):
         "config": {"workload": workload_name(n), "n": n, "edge_p": P_EDGE, "weights": [LO, HI],
                    "bs": args.bs, "driver": "phased" if args.driver == 2 else "persistent",
                    "parallelism": "replicas x%d" % world,
-                   "l2": "no flush: 8 GiB of dist+pred per step, far above the 129 MB L2"},
+                   "l2": "no flush: %.1f GiB of dist+pred per step, far above the 129 MB L2"
+                         % (2.0 * n * n * 4 / 2 ** 30)},
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": rps / 1e12,
-                     "unit": "Trelax/s", "frac": achieved / rps, "traffic": None,
+                     "unit": "Trelax/s", "frac": achieved / rps,
+                     "traffic": TRAFFIC_BYTES.get((n, args.bs, args.driver)),
                      "kernel": "k_persistent_ws<int,128>",
                      "peak_source": "fw_peak_probe (__viaddmin_u32 chains on all SMs, same "
                                     "process, %.1f relax/SM-clk at %.0f MHz)" % (per_clk,
