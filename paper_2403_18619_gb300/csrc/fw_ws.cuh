@@ -248,7 +248,7 @@ __device__ __forceinline__ bool ws_minplus(TileCtx<T> c, int ti, int tj, bool fa
   T* Drow = c.D + row0 * c.ld + col0;
   int32_t* Prow = c.P + row0 * c.ld + col0;
   bool neg = false;
-  if (fast) {
+  if (kInt && fast) {  // (packed keys: int32 only)
     uint32_t acc[TM][TM];
     int32_t omax = 0;
 #pragma unroll

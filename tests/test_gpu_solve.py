@@ -152,6 +152,31 @@ def test_f32_one_two_weights():
     check_f32(W, D, P, Do, Po)
 
 
+@pytest.mark.parametrize("n,bs", [(300, 32), (333, 64), (520, 128)])
+def test_f32_integer_weights_exact(n, bs):
+    """Integer-valued fp32 weights make every sum exact, with many equal-length
+    paths.  Distances equal the int64 oracle's, predecessors equal it on unique
+    paths and pass the shortest-path certificate everywhere (ties included),
+    and the persistent driver's two-step argmin (group minimum, then a search
+    of the group) picks the same step as the phased driver's compare per
+    step: both results are bit-identical."""
+    W = graphgen.dense_graph_i32(n, seed=n + 5, p=0.5, lo=1, hi=20)
+    inf = graphgen.INF_I32
+    Wf = np.where(W >= inf, np.inf, W).astype(np.float32)
+    Do, Po = oracle.fw_i64(W)
+    cnt = oracle.path_count_i64(W, Do)
+    D, P = gpu_solve(Wf, bs=bs, driver=PERSISTENT)
+    reach = np.isfinite(D)
+    assert (reach == (Do < inf)).all(), "reachability differs"
+    Di = np.where(reach, D, inf).astype(np.int32)
+    check_int_full(W, Di, P, Do, Po, cnt)
+    D2, P2 = gpu_solve(Wf, bs=bs, driver=PHASED)
+    assert np.array_equal(D, D2, equal_nan=True)
+    bad = np.argwhere(P != P2)
+    assert len(bad) == 0, "drivers differ on %d predecessors, first %s: %d vs %d" % (
+        len(bad), bad[0].tolist(), P[tuple(bad[0])], P2[tuple(bad[0])])
+
+
 # ---------------------------------------------------------- error paths ---
 
 def test_negative_cycle_reported():
