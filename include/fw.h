@@ -139,7 +139,10 @@ fw_status fw_solve_ex(void* dist, int32_t* pred, int64_t n, int64_t ld, fw_dtype
  * gives full copy bandwidth; pageable
  * memory works too.  Synchronous: returns after the results are on the host,
  * with any device-side error (as fw_sync_status would report it).  Device
- * buffers are cached per (device, stream) like the workspace.
+ * buffers are cached per (device, stream) like the workspace.  The distances
+ * are copied back on an internal stream as soon as they are final, while the
+ * int32 solve's predecessor pass still runs; opt->ev_stop, when given, is the
+ * event that marks that point.
  */
 fw_status fw_solve_host(void* dist_host, int32_t* pred_host, int64_t n, int64_t ld,
                         fw_dtype dtype, const fw_options* opt, void* stream);

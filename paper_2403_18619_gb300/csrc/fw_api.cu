@@ -25,6 +25,8 @@ struct StreamWs {
   void* hd = nullptr;
   void* hp = nullptr;
   size_t hbytes = 0;
+  cudaStream_t side = nullptr;     // copies dist back while pred is still resolved
+  cudaEvent_t ev_solved = nullptr, ev_side = nullptr;
   int* status = nullptr;  // sticky status word of this stream (lives in `sbase`)
   void* sbase = nullptr;
   void* bwd = nullptr;    // backward scratch (subtree sums)
@@ -333,6 +335,11 @@ fw_status fw_solve_host(void* dist_host, int32_t* pred_host, int64_t n, int64_t 
   const size_t bytes = (size_t)n * ld * 4;
   void* dd = nullptr;
   void* dp = nullptr;
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_side = nullptr;
+  fw_options o;
+  if (opt) o = *opt;
+  else fw_options_default(&o);
   {
     std::lock_guard<std::mutex> lk(g_mu);
     int dev = 0;
@@ -349,17 +356,33 @@ fw_status fw_solve_host(void* dist_host, int32_t* pred_host, int64_t n, int64_t 
       }
       w.hbytes = bytes;
     }
+    if (!w.side) {
+      if (cudaStreamCreateWithFlags(&w.side, cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&w.ev_solved, cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&w.ev_side, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        return FW_ERR_CUDA;
+      }
+    }
     dd = w.hd;
     dp = w.hp;
+    side = w.side;
+    ev_side = w.ev_side;
+    o.ev_stop = o.ev_stop ? o.ev_stop : reinterpret_cast<void*>(w.ev_solved);
   }
   if (cudaMemcpyAsync(dd, dist_host, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
     return FW_ERR_CUDA;
   fw_status st = fw_solve_ex(dd, pred_host ? reinterpret_cast<int32_t*>(dp) : nullptr, n, ld,
-                             dtype, opt, stream);
+                             dtype, &o, stream);
   if (st != FW_OK) return st;
-  if (cudaMemcpyAsync(dist_host, dd, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+  // The distances are final at ev_stop (the int32 solve's last pass rewrites
+  // only pred): they leave on the side stream while that pass runs.
+  if (cudaStreamWaitEvent(side, reinterpret_cast<cudaEvent_t>(o.ev_stop), 0) != cudaSuccess ||
+      cudaMemcpyAsync(dist_host, dd, bytes, cudaMemcpyDeviceToHost, side) != cudaSuccess ||
+      cudaEventRecord(ev_side, side) != cudaSuccess ||
       (pred_host &&
-       cudaMemcpyAsync(pred_host, dp, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess))
+       cudaMemcpyAsync(pred_host, dp, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) ||
+      cudaStreamWaitEvent(s, ev_side, 0) != cudaSuccess)
     return FW_ERR_CUDA;
   return fw_sync_status(stream);
 }
@@ -375,6 +398,9 @@ fw_status fw_release_workspace(void) {
       if (w.base) cudaFree(w.base);
       if (w.hd) cudaFree(w.hd);
       if (w.hp) cudaFree(w.hp);
+      if (w.side) cudaStreamDestroy(w.side);
+      if (w.ev_solved) cudaEventDestroy(w.ev_solved);
+      if (w.ev_side) cudaEventDestroy(w.ev_side);
       if (w.sbase) cudaFree(w.sbase);
       if (w.bwd) cudaFree(w.bwd);
       it = g_ws.erase(it);

@@ -132,6 +132,36 @@ def test_host_buffer_path():
     assert (Dh[:, 333:] == -5).all()
 
 
+@pytest.mark.parametrize("dtype", ["i32", "f32"])
+def test_host_buffer_path_events_and_repeats(dtype):
+    """The host path with the caller's own start/stop events (the stop event
+    also orders the early copy-back of the distances), on a non-default
+    stream, solved twice into the same buffers."""
+    import torch
+    m = fw()
+    n = 300
+    if dtype == "i32":
+        W, Do, Po, cnt = int_case(n, 8, 0.5, 1, 50)
+    else:
+        W = graphgen.dense_graph_f32(n, seed=8, p=0.5)
+        Do, Po = oracle.fw_f64(W)
+    s = torch.cuda.Stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    e1.record(s)
+    s.synchronize()
+    for _ in range(2):
+        Dh = np.array(W)
+        Ph = np.full((n, n), 7, np.int32)
+        opt = m.Options.default(bs=32, ev_start=e0.cuda_event, ev_stop=e1.cuda_event)
+        m.fw_solve_host(Dh, Ph, opt, s)
+        if dtype == "i32":
+            check_int_full(W, Dh, Ph, Do, Po, cnt)
+        else:
+            check_f32(W, Dh, Ph, Do, Po)
+        assert e0.elapsed_time(e1) > 0
+
+
 # ------------------------------------------------------------------- fp32 ---
 
 @pytest.mark.parametrize("driver", [PERSISTENT, PHASED])
