@@ -287,7 +287,7 @@ def bench_backward(fw, args):
             "speedup_vs_one_launch_per_graph": t_single / (fwd + bwd)}
 
 
-def bench_configs(fw, args):
+def bench_configs(fw, args, only=None):
     """The other single-graph workloads: n = 1024 complete digraph, int32
     U[1,100], BS = 32 (launch / latency-bound), and n = 8192, p = 0.5, as fp32
     (0,1] (with and without predecessors) and as int32 U[1,1000], each
@@ -301,6 +301,8 @@ def bench_configs(fw, args):
              ("n8192_f32_p0.5", 8192, fw.FW_F32, 0.5, 0, dict(kind=0), 2, True),
              ("n8192_f32_p0.5_distance_only", 8192, fw.FW_F32, 0.5, 0, dict(kind=0), 2, False)]
     for name, n, dt, p, bs, gen, seed, with_pred in cases:
+        if only is not None and name != only:
+            continue
         ld = fw.padded(n)
         tdt = torch.int32 if dt == fw.FW_I32 else torch.float32
         W = torch.empty((n, ld), dtype=tdt, device="cuda")
@@ -483,9 +485,22 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched and backward measurements")
+    ap.add_argument("--config", default=None,
+                    help="time only this one of the other single-graph workloads "
+                         "(n1024_i32_bs32, n8192_i32_p0.5, n8192_f32_p0.5, "
+                         "n8192_f32_p0.5_distance_only) and print its result, e.g. to profile it")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.config:
+        import torch
+        import paper_2403_18619_gb300 as fw
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        res = bench_configs(fw, args, only=args.config)
+        if not res:
+            raise SystemExit("unknown --config %r" % args.config)
+        print(json.dumps({"config": args.config, **res[args.config]}), flush=True)
+        return 0
     return run_gpu(args)
 
 
