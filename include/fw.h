@@ -82,7 +82,8 @@ typedef struct fw_options {
   int32_t bs;                 /* block size BS (Sec. 2.3): 0 = automatic, else 32, 64 or 128 */
   int32_t driver;             /* fw_driver */
   int32_t lookahead;          /* persistent driver: remaining-block tasks of round r queued
-                                 between the pivot and the panels of round r+1; -1 = automatic */
+                                 between the pivot and the panels of round r+1; -1 = automatic
+                                 (six per CTA, fewer when a round has few tasks) */
   int32_t grid;               /* persistent driver: CTAs; 0 = every co-resident CTA */
   int64_t timeout_ns;         /* bound on one device-side dependency wait; 0 = 2 s */
   int32_t packed_keys;        /* int32 only: 1 (default) relaxes packed (distance, pivot) keys

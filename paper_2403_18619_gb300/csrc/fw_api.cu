@@ -182,7 +182,7 @@ fw_status solve_device(void* dist, int32_t* pred, int64_t n, int64_t ld, fw_dtyp
   if (R64 > 1024) return FW_ERR_UNSUPPORTED;
   const int R = (int)R64;
   int64_t look = o.lookahead;
-  if (look < 0) look = (int64_t)2 * num_sms();
+  if (look < 0) look = auto_lookahead(R, num_sms());
 
   std::lock_guard<std::mutex> lk(g_mu);
   StreamWs* w = nullptr;

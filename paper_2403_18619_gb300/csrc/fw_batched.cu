@@ -196,10 +196,11 @@ fw_status plan_build(fw_batched_plan* p) {
   std::vector<std::vector<unsigned>> offs(B);
   int maxR = 0;
   int64_t total = 0;
-  const int64_t look = 2 * (int64_t)num_sms();
+  std::vector<int64_t> look(B);
   for (int64_t g = 0; g < B; ++g) {
+    look[g] = auto_lookahead(p->R[g], num_sms());
     offs[g].resize(p->R[g] + 2);
-    fill_stage_offsets(p->R[g], look, offs[g].data());
+    fill_stage_offsets(p->R[g], look[g], offs[g].data());
     maxR = std::max(maxR, p->R[g]);
     total += (int64_t)p->R[g] * p->R[g] * p->R[g];
   }
@@ -252,7 +253,7 @@ fw_status plan_build(fw_batched_plan* p) {
     a.abort_flag = p->d_abort;
     a.status = nullptr;
     a.stage_off = w.stage_off;
-    a.lookahead = (int)look;
+    a.lookahead = (int)look[g];
     a.skip_task = -1;
     a.timeout_ns = p->opt.timeout_ns > 0 ? p->opt.timeout_ns : 2000000000LL;
     a.packed = p->opt.packed_keys ? 1 : 0;

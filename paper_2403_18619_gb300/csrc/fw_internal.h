@@ -30,6 +30,19 @@ __host__ __device__ inline int64_t size_L(int R, int r) { return (r + 1 < R) ? 2
 __host__ __device__ inline int64_t size_rest(int R, int r) {
   return (int64_t)(R - 1) * (R - 1) - size_L(R, r);
 }
+// Automatic lookahead g for `sms` co-resident CTAs: enough remaining tiles
+// of round s-1 ahead of the panels of round s that the panels are claimed as
+// the pivot finishes (its inputs' wait plus the pivot itself last about six
+// BS = 128 remaining-tile tasks; claimed earlier, a panel task idles its SM
+// until then), while leaving at least three tasks per CTA behind the panels
+// to cover their own latency before round s's remaining tiles need them.
+__host__ __device__ inline int64_t auto_lookahead(int R, int sms) {
+  const int64_t nrest = size_rest(R, 0);
+  int64_t g = nrest - 3 * (int64_t)sms;
+  if (g > 6 * (int64_t)sms) g = 6 * (int64_t)sms;
+  if (g < 2 * (int64_t)sms) g = 2 * (int64_t)sms;
+  return g;
+}
 __host__ __device__ inline int64_t stage_size(int R, int s, int64_t look) {
   if (s == 0) return 1 + 2 * (int64_t)(R - 1) + size_L(R, 0);
   if (s == R) return size_rest(R, R - 1);

@@ -55,7 +55,7 @@ cudaError_t run(T* D, int32_t* P, int64_t n, int64_t ld, unsigned char* base, in
                 cudaStream_t s) {
   using namespace fwk;
   const int R = (int)((n + BS - 1) / BS);
-  const int64_t look = 2 * (int64_t)sms;
+  const int64_t look = fwh::auto_lookahead(R, sms);
   int* status = reinterpret_cast<int*>(base);
   fwh::SolveWs ws = fwh::carve_solve_ws(base + kStatusBytes, R, BS);
   cudaError_t e;

@@ -187,9 +187,9 @@ def test_f32_integer_weights_exact(n, bs):
     """Integer-valued fp32 weights make every sum exact, with many equal-length
     paths.  Distances equal the int64 oracle's, predecessors equal it on unique
     paths and pass the shortest-path certificate everywhere (ties included),
-    and the persistent driver's two-step argmin (group minimum, then a search
-    of the group) picks the same step as the phased driver's compare per
-    step: both results are bit-identical."""
+    and the persistent and phased drivers (different task orders, snapshots
+    and kernels for the remaining tiles) give bit-identical results: both
+    keep the first step that reaches each minimum."""
     W = graphgen.dense_graph_i32(n, seed=n + 5, p=0.5, lo=1, hi=20)
     inf = graphgen.INF_I32
     Wf = np.where(W >= inf, np.inf, W).astype(np.float32)
@@ -242,7 +242,8 @@ def test_dependency_timeout_is_reported_not_hung():
     ld = m.padded(n)
     D = torch.from_numpy(W).cuda()
     P = torch.empty_like(D)
-    opt = m.Options.default(bs=32, debug_skip_release=skip, timeout_ns=200_000_000)
+    opt = m.Options.default(bs=32, lookahead=2 * 152, debug_skip_release=skip,
+                            timeout_ns=200_000_000)
     m.fw_solve_ex(D, P, opt)
     with pytest.raises(m.FWError) as e:
         m.fw_sync_status()
