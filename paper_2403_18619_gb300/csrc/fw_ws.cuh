@@ -306,7 +306,6 @@ __device__ __forceinline__ bool ws_minplus(TileCtx<T> c, int ti, int tj, bool fa
               dv[e] = (T)(int32_t)(kv >> K::KB);
             }
             if (cg) vstore<G>(Drow + lr * c.ld + lc0, dv);
-#pragma unroll
             if (c.P) {
 #pragma unroll
               for (int e = 0; e < G; ++e) {
