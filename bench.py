@@ -166,6 +166,25 @@ def run_reference(args):
     return 0
 
 
+# ----------------------------------------------------------- across ranks ---
+
+def reduce_max(x: float, world: int, device="cuda") -> float:
+    """Maximum of x over the ranks (x itself when there is one rank)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, t_max_s: float) -> float:
+    """Units all ranks processed per second of the slowest rank (weak scaling:
+    every rank runs the same workload on its own instance)."""
+    return world * units_per_rank / t_max_s
+
+
 # ------------------------------------------------------------------- GPU ---
 
 def _events(k):
@@ -396,13 +415,9 @@ def run_gpu(args):
         dist.barrier()
     step_ms = [ev0[i].elapsed_time(ev1[i]) for i in range(args.steps)]
     kern_ms = [k0[i].elapsed_time(k1[i]) for i in range(args.steps)]
-    t_ms = sum(step_ms)
-    if world > 1:
-        tt = torch.tensor([t_ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_ms = float(tt.item())
+    t_ms = reduce_max(sum(step_ms), world)
     relax = float(n) ** 3
-    value = world * relax * args.steps / (t_ms * 1e-3)
+    value = whole_job_rate(relax * args.steps, world, t_ms * 1e-3)
 
     # end to end through the host-buffer entry point (pinned memory, copies timed)
     e2e = None
@@ -420,8 +435,8 @@ def run_gpu(args):
             dt = time.perf_counter() - t0
             if i > 0:
                 times.append(dt)
-        te = sum(times) / len(times)
-        e2e = {"value": world * relax / te, "unit": "relax/s",
+        te = reduce_max(sum(times) / len(times), world)
+        e2e = {"value": whole_job_rate(relax, world, te), "unit": "relax/s",
                "h2d_bytes_per_step": n * ld * 4, "d2h_bytes_per_step": 2 * n * ld * 4,
                "ms_per_step": te * 1e3, "api": "fw_solve_host (pinned host buffers)"}
 
