@@ -79,7 +79,8 @@ typedef enum {
 } fw_driver;
 
 typedef struct fw_options {
-  int32_t bs;                 /* block size BS (Sec. 2.3): 0 = automatic, else 32, 64 or 128 */
+  int32_t bs;                 /* block size BS (Sec. 2.3): 0 = automatic (32 up to n = 512,
+                                 64 up to 3072, else 128), else 32, 64 or 128 */
   int32_t driver;             /* fw_driver */
   int32_t lookahead;          /* persistent driver: remaining-block tasks of round r queued
                                  between the pivot and the panels of round r+1; -1 = automatic

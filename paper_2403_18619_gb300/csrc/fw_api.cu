@@ -122,9 +122,14 @@ SolveWs carve_solve_ws(void* base, int R, int BS) {
   return w;
 }
 
+// Automatic BS of a single solve.  Larger blocks relax faster (BS = 128 runs
+// the DPX loop at ~84 % of peak, BS = 64 at ~50 %) but make R = n / BS rounds
+// whose pivot -> panel chain is longer; measured on GB300 (int32, persistent
+// driver): n = 2048 BS 64 1.27 ms vs BS 128 2.16 ms; n = 4096 BS 64 7.70 ms vs
+// BS 128 5.91 ms.  The two costs cross near n = 3072.
 int pick_bs(int64_t n) {
   if (n <= 512) return 32;
-  if (n <= 4096) return 64;
+  if (n <= 3072) return 64;
   return 128;
 }
 
