@@ -8,7 +8,7 @@
  * weights and in fp64 for real weights (inputs are read as int32 / fp32 and
  * widened).  OpenMP only splits loops whose iterations are independent.
  *
- * Conventions (the paper's reading, see the design notes):
+ * Conventions (readings of points the paper leaves open):
  *   - A missing edge is `inf` (int path) or +infinity (real path).  A path
  *     through an unreachable vertex does not exist, so it is never compared.
  *   - D[i][i] = 0 on input (the diagonal of a distance matrix).
