@@ -106,6 +106,36 @@ def test_int_zero_weight_edges():
     assert cert[0] == 0 and cert[1] == 0 and cert[2] == 0
 
 
+def test_task_trace_covers_every_task_in_order():
+    """A traced persistent solve: one row per task, the queue's task mix, each
+    task's timeline in causal order (claimed <= inputs ready <= compute start
+    <= compute end <= published), and the solve itself still exact."""
+    import torch
+    from paper_2403_18619_gb300 import tracing
+    m = fw()
+    n, bs = 1000, 128
+    R = (n + bs - 1) // bs
+    W, Do, Po, cnt = int_case(n, 61, 0.5, 1, 90)
+    tr = torch.zeros((R ** 3, 10), dtype=torch.int64, device="cuda")
+    D = torch.from_numpy(W).cuda()
+    P = torch.empty_like(D)
+    opt = m.Options.default(bs=bs, driver=PERSISTENT, trace=tr.data_ptr(), trace_cap=R ** 3,
+                            trace_stride=1)
+    m.fw_solve_ex(D, P, opt)
+    m.fw_sync_status()
+    check_int_full(W, D.cpu().numpy(), P.cpu().numpy(), Do, Po, cnt)
+    d = tracing.decode(tr.cpu().numpy())
+    assert sorted(d["task"].tolist()) == list(range(R ** 3))
+    counts = np.bincount(d["type"], minlength=4).tolist()
+    assert counts == [R, R * (R - 1), R * (R - 1), R * (R - 1) ** 2]
+    assert (d["claimed"] <= d["ready"]).all()
+    assert (d["ready"] <= d["start"]).all()
+    assert (d["start"] <= d["end"]).all()
+    assert (d["end"] <= d["published"]).all()
+    s = tracing.summarize(tr.cpu().numpy())
+    assert s["tasks"] == R ** 3 and 0 < s["busy_fraction"]["mean"] <= 1
+
+
 def test_repeated_solves_share_workspace():
     cases = [int_case(n, 50 + n, 0.5, 1, 30) for n in (200, 520, 64)]
     for W, Do, Po, cnt in cases + cases[:1]:

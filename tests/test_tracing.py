@@ -1,0 +1,66 @@
+"""The task-trace decoder on a hand-built trace (no GPU)."""
+import numpy as np
+import pytest
+
+from paper_2403_18619_gb300 import tracing
+
+
+def _row(task, typ, sm, claimed, ready, issued, start, end, published, c7=0, c8=0):
+    return [task | (typ << 32), sm, claimed, ready, issued, published, start, c7, c8, end]
+
+
+def _trace():
+    rows = [
+        # pivot on SM 0: waits 2 us for its tile, computes 10 us
+        _row(0, 0, 0, 1000, 3000, 3000, 3500, 13500, 14000,
+             c7=100 | (900 << 32), c8=1000 | (1200 << 32)),
+        # remaining tile on SM 1: 5 us compute
+        _row(7, 3, 1, 1000, 1500, 1600, 2000, 7000, 7500,
+             c7=30 | (40 << 20) | (5 << 40), c8=9000 | (10000 << 32)),
+        # a second remaining tile on SM 1, 1 us after the first
+        _row(8, 3, 1, 6000, 6500, 6600, 8000, 12000, 12500,
+             c7=10 | (20 << 20) | (0 << 40), c8=8000 | (9000 << 32)),
+    ]
+    t = np.zeros((6, 10), np.uint64)   # cap above the tasks written: zero rows are skipped
+    t[:3] = np.array(rows, dtype=np.uint64)
+    return t
+
+
+def test_decode_fields():
+    d = tracing.decode(_trace())
+    assert d["task"].tolist() == [0, 7, 8]
+    assert d["type"].tolist() == [0, 3, 3]
+    assert d["sm"].tolist() == [0, 1, 1]
+    assert d["tile_wait"].tolist()[1:] == [30, 10]
+    assert d["chunk_wait"].tolist()[1:] == [40, 20]
+    assert d["pred_wait"].tolist()[1:] == [5, 0]
+    assert d["relax_end"].tolist()[1:] == [9000, 8000]
+    assert d["whole"].tolist() == [1200, 10000, 9000]
+    assert d["loaded"][0] == 100 and d["relaxed"][0] == 900 and d["stored"][0] == 1000
+
+
+def test_summary():
+    s = tracing.summarize(_trace())
+    assert s["tasks"] == 3
+    assert s["span_us"] == pytest.approx((14000 - 1000) / 1e3)
+    piv = s["types"]["pivot"]
+    assert piv["compute_us"]["mean"] == pytest.approx(10.0)
+    assert piv["input_wait_us"]["mean"] == pytest.approx(2.0)
+    assert piv["publish_lag_us"]["mean"] == pytest.approx(0.5)
+    assert piv["cycles"] == {"loads": 100.0, "relax": 800.0, "post": 100.0, "store_end": 200.0,
+                             "whole": 1200.0}
+    rem = s["types"]["remaining"]
+    assert rem["compute_us"]["n"] == 2 and rem["compute_us"]["mean"] == pytest.approx(4.5)
+    assert rem["cycles"]["relax"] == pytest.approx(((9000 - 70) + (8000 - 30)) / 2)
+    assert rem["cycles"]["epilogue"] == pytest.approx(((10000 - 9000 - 5) + (9000 - 8000)) / 2)
+    # SM 0 busy 10 us of 13, SM 1 busy 9 us of 13; one gap of 1 us on SM 1
+    assert s["busy_fraction"]["sms"] == 2
+    assert s["busy_fraction"]["min"] == pytest.approx(9 / 13)
+    assert s["busy_fraction"]["mean"] == pytest.approx((10 / 13 + 9 / 13) / 2)
+    assert s["gap_us"]["n"] == 1 and s["gap_us"]["mean"] == pytest.approx(1.0)
+
+
+def test_empty_and_bad_shapes():
+    assert tracing.summarize(np.zeros((4, 10), np.uint64)) == {"tasks": 0}
+    with pytest.raises(ValueError):
+        tracing.decode(np.zeros((4, 9), np.uint64))
