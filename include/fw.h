@@ -280,6 +280,19 @@ fw_status fw_solve_noalloc(void* dist, int32_t* pred, int64_t n, int64_t ld, fw_
                            void* stream);
 
 /*
+ * fw_solve_plan: what fw_solve_ex would choose for n vertices and *opt (NULL:
+ * defaults) on a GPU with `sms` co-resident CTAs (one per SM): the block size
+ * BS, the number of rounds R = ceil(n / BS) (Sec. 2.3), the lookahead of the
+ * persistent queue, and the bytes of device workspace it keeps per (device,
+ * stream) besides the caller's matrices (tile versions, queue offsets, pivot
+ * and panel snapshots).  Any output pointer may be NULL.  Host only: no CUDA
+ * call.  FW_ERR_ARG for n outside [1, 131072], sms < 1 or invalid options;
+ * FW_ERR_UNSUPPORTED when R would exceed 1024.
+ */
+fw_status fw_solve_plan(int64_t n, const fw_options* opt, int32_t sms, int32_t* bs,
+                        int32_t* rounds, int64_t* lookahead, int64_t* workspace_bytes);
+
+/*
  * fw_queue_tasks: diagnostic view of the persistent driver's task queue for R
  * tile rows (R = ceil(n / BS)) and a given lookahead (the value fw_options
  * .lookahead resolves to).  Writes 4 int32 per task -- type (0 pivot, 1 row

@@ -99,6 +99,7 @@ def load():
         lib.fw_peak_probe.argtypes = [I32, P, P, P, P]
         lib.fw_verify_certificate.argtypes = [P, P, P, I64, I64, P, P]
         lib.fw_queue_tasks.argtypes = [I32, I64, I64, I64, P]
+        lib.fw_solve_plan.argtypes = [I64, P, I32, P, P, P, P]
         lib.fw_solve_noalloc.argtypes = [P, P, I64, I64, I32, P]
         lib.fw_bs_table.argtypes = [P, I32]
         lib.fw_autotune_bs.argtypes = [I32, I64, I64, P, P, P]
@@ -106,7 +107,8 @@ def load():
                      "fw_solve_batched", "fw_batched_plan_info", "fw_batched_plan_destroy",
                      "fw_backward", "fw_backward_strided", "fw_sync_status",
                      "fw_release_workspace", "fw_peak_probe", "fw_verify_certificate",
-                     "fw_queue_tasks", "fw_solve_noalloc", "fw_bs_table", "fw_autotune_bs"):
+                     "fw_queue_tasks", "fw_solve_noalloc", "fw_bs_table", "fw_autotune_bs",
+                     "fw_solve_plan"):
             getattr(lib, name).restype = I32
         _lib = lib
         return lib
@@ -253,6 +255,18 @@ def fw_verify_certificate(W, dist, pred, stream=None) -> np.ndarray:
     check(load().fw_verify_certificate(wp, dp, pp, n, ld, bad.ctypes.data, _stream_ptr(stream)),
           "fw_verify_certificate")
     return bad
+
+
+def fw_solve_plan(n: int, options: Options | None = None, sms: int = 152) -> dict:
+    """What fw_solve_ex would choose for n vertices on a GPU with `sms` SMs:
+    block size, rounds, queue lookahead and device workspace bytes (host only)."""
+    bs, rounds = ctypes.c_int32(), ctypes.c_int32()
+    look, ws = ctypes.c_int64(), ctypes.c_int64()
+    o = ctypes.byref(options) if options is not None else None
+    check(load().fw_solve_plan(n, o, sms, ctypes.byref(bs), ctypes.byref(rounds),
+                               ctypes.byref(look), ctypes.byref(ws)), "fw_solve_plan")
+    return {"bs": bs.value, "rounds": rounds.value, "lookahead": look.value,
+            "workspace_bytes": ws.value}
 
 
 def fw_queue_tasks(R: int, lookahead: int, first: int = 0, count: int | None = None) -> np.ndarray:

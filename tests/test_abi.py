@@ -144,3 +144,25 @@ def test_bs_table_host(fw):
         fw.fw_bs_table(np.array([32, 32, 48, 64, 128, 128, 128], np.int32))
     fw.fw_bs_table(t)
     assert (fw.fw_bs_table() == t).all()
+
+
+def test_solve_plan_choices(fw):
+    """fw_solve_plan (host only): the automatic block size and lookahead, the
+    rounds and the workspace a solve keeps, and its argument checks."""
+    p = fw.fw_solve_plan(32768, sms=152)
+    assert p["bs"] == 128 and p["rounds"] == 256 and p["lookahead"] == 6 * 152
+    # snapshots dominate: 2 slots x R x BS^2 x 4 B x 5 arrays = 160 MiB (+ flags, offsets)
+    assert 5 * 2 * 256 * 128 * 128 * 4 <= p["workspace_bytes"] < 170 * 2 ** 20
+    assert fw.fw_solve_plan(512)["bs"] == 32
+    assert fw.fw_solve_plan(3072)["bs"] == 64 and fw.fw_solve_plan(3073)["bs"] == 128
+    # few tasks per round: at least 3 x SMs stay behind the panels, at least 2 x SMs ahead
+    p = fw.fw_solve_plan(4096, fw.Options.default(bs=128), sms=152)
+    assert p["rounds"] == 32 and p["lookahead"] == 31 * 31 - 61 - 3 * 152
+    p = fw.fw_solve_plan(1024, fw.Options.default(bs=128), sms=152)
+    assert p["lookahead"] == 2 * 152
+    assert fw.fw_solve_plan(8192, fw.Options.default(lookahead=77))["lookahead"] == 77
+    lib = fw.load()
+    assert lib.fw_solve_plan(0, None, 152, None, None, None, None) == 1
+    assert lib.fw_solve_plan(100, None, 0, None, None, None, None) == 1
+    assert lib.fw_solve_plan(131072, ctypes.byref(fw.Options.default(bs=32)), 152,
+                             None, None, None, None) == 6
