@@ -15,9 +15,12 @@ import threading
 import numpy as np
 
 __all__ = [
-    "FWError", "Options", "load", "fw_solve", "fw_solve_ex", "fw_solve_host", "fw_sync_status",
-    "fw_peak_probe", "fw_verify_certificate", "fw_release_workspace", "solve", "check",
-    "INF_I32", "FW_I32", "FW_F32", "DRIVER_AUTO", "DRIVER_PERSISTENT", "DRIVER_PHASED",
+    "FWError", "Options", "load", "check", "fw_solve", "fw_solve_ex", "fw_solve_host",
+    "fw_solve_noalloc", "fw_sync_status", "fw_backward", "fw_backward_strided",
+    "fw_peak_probe", "fw_verify_certificate", "fw_release_workspace", "fw_solve_plan",
+    "fw_queue_tasks", "BatchedPlan", "fw_bs_table", "fw_autotune_bs", "padded", "solve",
+    "solve_batched", "INF_I32", "FW_I32", "FW_F32", "DRIVER_AUTO", "DRIVER_PERSISTENT",
+    "DRIVER_PHASED",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
