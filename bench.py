@@ -179,6 +179,14 @@ def reduce_max(x: float, world: int, device="cuda") -> float:
     return float(t.item())
 
 
+def step_stats(ms) -> dict:
+    """Mean, median, min and max of this rank's timed steps (ms), the spread
+    behind the single rate of the line."""
+    ms = [float(x) for x in ms]
+    return {"mean": statistics.fmean(ms), "median": statistics.median(ms), "min": min(ms),
+            "max": max(ms), "n": len(ms)}
+
+
 def whole_job_rate(units_per_rank: float, world: int, t_max_s: float) -> float:
     """Units all ranks processed per second of the slowest rank (weak scaling:
     every rank runs the same workload on its own instance)."""
@@ -472,6 +480,7 @@ def run_gpu(args):
         "clocks": clocks.summary(),
         "gpu_launches": 3 * args.steps,  # init, persistent solver, predecessor resolution
         "wall_s_timed_region": wall,
+        "step_ms_stats": step_stats(step_ms),
     }
     if e2e:
         line["e2e"] = e2e

@@ -85,3 +85,10 @@ def test_reference_arm_line_on_rank_zero():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 4
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
     assert d["metric"] == "relaxations/s (n^3/t)" and d["higher_is_better"] is True
+
+
+def test_step_stats():
+    sys.path.insert(0, ROOT)
+    import bench
+    s = bench.step_stats([3.0, 1.0, 2.0, 10.0])
+    assert s == {"mean": 4.0, "median": 2.5, "min": 1.0, "max": 10.0, "n": 4}
