@@ -280,6 +280,25 @@ fw_status fw_solve_noalloc(void* dist, int32_t* pred, int64_t n, int64_t ld, fw_
                            void* stream);
 
 /*
+ * fw_paths: the shortest paths that a solved predecessor matrix records
+ * (Sec. 2.3: P lets the paths be rebuilt), for a batch of (source, target)
+ * pairs, on the GPU.  pred: device, n x ld int32, as a solve with
+ * predecessors leaves it (last hops, -1 where there is none).  src, dst:
+ * device arrays of npairs vertex ids.  out: device, npairs x max_len int32;
+ * row q receives the vertices of the path from src[q] to dst[q] in order
+ * (src[q] first, dst[q] last).  len: device, npairs int32: the vertex count
+ * of each path (1 when src == dst), 0 when dst is unreachable from src, -1
+ * when an id is outside [0, n), the path has more than max_len vertices, or
+ * pred is not a tree of last hops (a walk would leave [0, n) or take more
+ * than n vertices); out row q is then unspecified.  Every walk is bounded by
+ * n hops.  Asynchronous on stream; FW_ERR_ARG for null pointers, n outside
+ * [1, 131072], ld < n, npairs < 0 or max_len < 1.
+ */
+fw_status fw_paths(const int32_t* pred, int64_t n, int64_t ld, const int32_t* src,
+                   const int32_t* dst, int64_t npairs, int32_t* out, int64_t max_len,
+                   int32_t* len, void* stream);
+
+/*
  * fw_solve_plan: what fw_solve_ex would choose for n vertices and *opt (NULL:
  * defaults) on a GPU with `sms` co-resident CTAs (one per SM): the block size
  * BS, the number of rounds R = ceil(n / BS) (Sec. 2.3), the lookahead of the

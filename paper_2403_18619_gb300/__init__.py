@@ -18,7 +18,7 @@ __all__ = [
     "FWError", "Options", "load", "check", "fw_solve", "fw_solve_ex", "fw_solve_host",
     "fw_solve_noalloc", "fw_sync_status", "fw_backward", "fw_backward_strided",
     "fw_peak_probe", "fw_verify_certificate", "fw_release_workspace", "fw_solve_plan",
-    "fw_queue_tasks", "BatchedPlan", "fw_bs_table", "fw_autotune_bs", "padded", "solve",
+    "fw_queue_tasks", "fw_paths", "BatchedPlan", "fw_bs_table", "fw_autotune_bs", "padded", "solve",
     "solve_batched", "INF_I32", "FW_I32", "FW_F32", "DRIVER_AUTO", "DRIVER_PERSISTENT",
     "DRIVER_PHASED",
 ]
@@ -103,6 +103,7 @@ def load():
         lib.fw_verify_certificate.argtypes = [P, P, P, I64, I64, P, P]
         lib.fw_queue_tasks.argtypes = [I32, I64, I64, I64, P]
         lib.fw_solve_plan.argtypes = [I64, P, I32, P, P, P, P]
+        lib.fw_paths.argtypes = [P, I64, I64, P, P, I64, P, I64, P, P]
         lib.fw_solve_noalloc.argtypes = [P, P, I64, I64, I32, P]
         lib.fw_bs_table.argtypes = [P, I32]
         lib.fw_autotune_bs.argtypes = [I32, I64, I64, P, P, P]
@@ -111,7 +112,7 @@ def load():
                      "fw_backward", "fw_backward_strided", "fw_sync_status",
                      "fw_release_workspace", "fw_peak_probe", "fw_verify_certificate",
                      "fw_queue_tasks", "fw_solve_noalloc", "fw_bs_table", "fw_autotune_bs",
-                     "fw_solve_plan"):
+                     "fw_solve_plan", "fw_paths"):
             getattr(lib, name).restype = I32
         _lib = lib
         return lib
@@ -258,6 +259,29 @@ def fw_verify_certificate(W, dist, pred, stream=None) -> np.ndarray:
     check(load().fw_verify_certificate(wp, dp, pp, n, ld, bad.ctypes.data, _stream_ptr(stream)),
           "fw_verify_certificate")
     return bad
+
+
+def fw_paths(pred, src, dst, max_len: int, stream=None):
+    """fw_paths on CUDA tensors: pred (n x n view of a solved predecessor
+    matrix), src / dst (int32 vectors of vertex ids).  Returns (paths, lengths):
+    paths[q, :lengths[q]] are the vertices from src[q] to dst[q]; lengths[q] is
+    0 when dst[q] is unreachable and -1 for an invalid request."""
+    import torch
+    pp, n, ld = _matrix(pred, "pred")
+    if pred.dtype != torch.int32:
+        raise TypeError("pred must be int32")
+    for name, v in (("src", src), ("dst", dst)):
+        if not isinstance(v, torch.Tensor) or not v.is_cuda or v.dtype != torch.int32 \
+                or v.dim() != 1 or not v.is_contiguous():
+            raise TypeError("%s must be a contiguous int32 CUDA vector" % name)
+    if src.numel() != dst.numel():
+        raise ValueError("src and dst must have the same length")
+    m = src.numel()
+    out = torch.empty((m, max(1, int(max_len))), dtype=torch.int32, device=pred.device)
+    lens = torch.empty((m,), dtype=torch.int32, device=pred.device)
+    check(load().fw_paths(pp, n, ld, src.data_ptr(), dst.data_ptr(), m, out.data_ptr(),
+                          int(max_len), lens.data_ptr(), _stream_ptr(stream)), "fw_paths")
+    return out, lens
 
 
 def fw_solve_plan(n: int, options: Options | None = None, sms: int = 152) -> dict:

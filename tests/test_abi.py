@@ -166,3 +166,16 @@ def test_solve_plan_choices(fw):
     assert lib.fw_solve_plan(100, None, 0, None, None, None, None) == 1
     assert lib.fw_solve_plan(131072, ctypes.byref(fw.Options.default(bs=32)), 152,
                              None, None, None, None) == 6
+
+
+def test_paths_argument_checks(fw):
+    """fw_paths rejects bad arguments on the host and launches nothing for an
+    empty batch (no GPU needed)."""
+    lib = fw.load()
+    p = ctypes.c_void_p(16)
+    assert lib.fw_paths(None, 10, 10, p, p, 1, p, 4, p, None) == 1
+    assert lib.fw_paths(p, 0, 10, p, p, 1, p, 4, p, None) == 1
+    assert lib.fw_paths(p, 10, 8, p, p, 1, p, 4, p, None) == 1
+    assert lib.fw_paths(p, 10, 10, p, p, -1, p, 4, p, None) == 1
+    assert lib.fw_paths(p, 10, 10, p, p, 1, p, 0, p, None) == 1
+    assert lib.fw_paths(p, 10, 10, p, p, 0, p, 4, p, None) == 0
