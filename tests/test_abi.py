@@ -77,9 +77,13 @@ def _update_task(t):
     return (r, i, j)
 
 
-@pytest.mark.parametrize("R", [1, 2, 3, 4, 7, 12])
-@pytest.mark.parametrize("look", [0, 5, 10 ** 6])
+@pytest.mark.parametrize("R,look", [(R, look) for R in (1, 2, 3, 4, 7, 12)
+                                    for look in (0, 5, 10 ** 6)] +
+                         [(32, "auto"), (24, "auto"), (40, "auto")])
 def test_queue_is_complete_and_topological(fw, R, look):
+    if look == "auto":
+        # the lookahead a BS = 128 solve with R rounds gets on 152 SMs
+        look = fw.fw_solve_plan(R * 128, fw.Options.default(bs=128), sms=152)["lookahead"]
     q = fw.fw_queue_tasks(R, look)
     assert q.shape == (R ** 3, 4)
     pos = {}
