@@ -38,10 +38,10 @@ P_EDGE = 0.9
 LO, HI = 1, 10_000
 BS = 128
 SAMPLE_N = 2048          # CPU baseline: leading 2048-vertex induced subgraph
-# DRAM bytes (read + write) of one k_persistent_ws launch, from one ncu
-# capture of this workload (profiles/k_persistent_ws_int32_n32768_launches.md);
-# algorithmic: 8 n^3 / BS = 2.20e12 B.  Other configurations: not captured.
-TRAFFIC_BYTES = {(32768, 128, 1): 1.53e12 + 0.66292e12}
+# DRAM bytes (read + write) of one k_persistent_ws launch of the current
+# kernel, keyed by (n, BS, driver); null in the line where no capture exists.
+# Algorithmic: 8 n^3 / BS = 2.20e12 B at n = 32768, BS = 128.
+TRAFFIC_BYTES = {}
 
 
 def workload_name(n=N_FULL):

@@ -271,7 +271,9 @@ fw_status fw_verify_certificate(const int32_t* W, const int32_t* dist, const int
  *
  * The first call on each device looks up the array's device address
  * (cudaGetSymbolAddress with that device current) and caches it; make that
- * first call before any stream capture on the device.  Every call, from any
+ * first call before any stream capture on the device.  The cached address
+ * does not survive cudaDeviceReset: calls after a reset of the device are not
+ * supported.  Every call, from any
  * thread or stream, uses the same array and clears the parts that must start
  * at zero; calls whose executions overlap on the GPU race on it and produce
  * wrong results, so serialise them (one at a time per device).

@@ -31,12 +31,15 @@ struct StreamWs {
   void* sbase = nullptr;
   void* bwd = nullptr;    // backward scratch (subtree sums)
   size_t bwd_bytes = 0;
+  std::mutex mu;          // guards this entry; taken after g_mu, never the other way round
 };
 
-std::mutex g_mu;       // guards g_ws
+std::mutex g_mu;       // guards the map g_ws (entries are guarded by their own mutex)
 std::mutex g_sms_mu;   // guards g_sms (taken on its own, also while g_mu is held)
 std::map<std::pair<int, cudaStream_t>, StreamWs> g_ws;
 std::map<int, int> g_sms;
+std::mutex g_ksetup_mu;  // guards g_ksetup (taken on its own, also while g_mu is held)
+std::map<std::pair<int, const void*>, int> g_ksetup;  // (device, kernel) -> CTAs per SM
 
 }  // namespace
 
@@ -87,6 +90,27 @@ int num_sms() {
   return v;
 }
 
+int kernel_setup(const void* fn, size_t smem, int threads) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+  std::lock_guard<std::mutex> lk(g_ksetup_mu);
+  auto it = g_ksetup.find({dev, fn});
+  if (it != g_ksetup.end()) return it->second;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, smem) != cudaSuccess ||
+      occ < 1) {
+    cudaGetLastError();
+    return -1;
+  }
+  g_ksetup[{dev, fn}] = occ;
+  return occ;
+}
+
 size_t solve_ws_bytes(int R, int BS) {
   const size_t t = (size_t)BS * BS;
   size_t b = 0;
@@ -133,11 +157,25 @@ int pick_bs(int64_t n) {
   return 128;
 }
 
-// Workspace for (current device, stream), grown to `need` bytes.  Caller holds g_mu.
-static fw_status get_ws(cudaStream_t s, size_t need, StreamWs** out) {
+// The workspace entry of (current device, stream), created if missing, locked
+// for the caller.  Host threads working on different streams hold different
+// entries and do not wait for each other.
+static std::unique_lock<std::mutex> lock_entry(cudaStream_t s, StreamWs** out) {
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return FW_ERR_CUDA;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    *out = nullptr;
+    return std::unique_lock<std::mutex>();
+  }
+  std::lock_guard<std::mutex> g(g_mu);
   StreamWs& w = g_ws[{dev, s}];
+  std::unique_lock<std::mutex> lk(w.mu);
+  *out = &w;
+  return lk;
+}
+
+// Grows the locked entry w of stream s to `need` bytes of solve workspace
+// (and creates its status word).
+static fw_status get_ws(StreamWs& w, cudaStream_t s, size_t need) {
   if (!w.sbase) {
     if (cudaMalloc(&w.sbase, 256) != cudaSuccess) return FW_ERR_NOMEM;
     if (cudaMemset(w.sbase, 0, 256) != cudaSuccess) return FW_ERR_CUDA;
@@ -157,7 +195,6 @@ static fw_status get_ws(cudaStream_t s, size_t need, StreamWs** out) {
     w.bytes = need;
     w.cached_R = -1;
   }
-  *out = &w;
   return FW_OK;
 }
 
@@ -189,9 +226,10 @@ fw_status solve_device(void* dist, int32_t* pred, int64_t n, int64_t ld, fw_dtyp
   int64_t look = o.lookahead;
   if (look < 0) look = auto_lookahead(R, num_sms());
 
-  std::lock_guard<std::mutex> lk(g_mu);
   StreamWs* w = nullptr;
-  fw_status st = get_ws(s, solve_ws_bytes(R, BS), &w);
+  auto lk = lock_entry(s, &w);
+  if (!w) return FW_ERR_CUDA;
+  fw_status st = get_ws(*w, s, solve_ws_bytes(R, BS));
   if (st != FW_OK) return st;
   SolveWs ws = carve_solve_ws(w->base, R, BS);
   ws.status = w->status;
@@ -227,10 +265,10 @@ fw_status solve_device(void* dist, int32_t* pred, int64_t n, int64_t ld, fw_dtyp
 
 // Backward scratch of (current device, stream), grown to `bytes`.
 void* backward_scratch(cudaStream_t s, size_t bytes) {
-  std::lock_guard<std::mutex> lk(g_mu);
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
-  StreamWs& w = g_ws[{dev, s}];
+  StreamWs* wp = nullptr;
+  auto lk = lock_entry(s, &wp);
+  if (!wp) return nullptr;
+  StreamWs& w = *wp;
   if (w.bwd_bytes < bytes) {
     if (w.bwd) {
       cudaStreamSynchronize(s);
@@ -249,9 +287,9 @@ void* backward_scratch(cudaStream_t s, size_t bytes) {
 
 // Status word of (current device, stream), created if the stream has none yet.
 int* status_word_for(cudaStream_t s) {
-  std::lock_guard<std::mutex> lk(g_mu);
   StreamWs* w = nullptr;
-  if (get_ws(s, 0, &w) != FW_OK) return nullptr;
+  auto lk = lock_entry(s, &w);
+  if (!w || get_ws(*w, s, 0) != FW_OK) return nullptr;
   return w->status;
 }
 
@@ -261,7 +299,9 @@ int* stream_status(cudaStream_t s) {
   cudaGetDevice(&dev);
   std::lock_guard<std::mutex> lk(g_mu);
   auto it = g_ws.find({dev, s});
-  return it == g_ws.end() ? nullptr : it->second.status;
+  if (it == g_ws.end()) return nullptr;
+  std::lock_guard<std::mutex> lk2(it->second.mu);
+  return it->second.status;
 }
 
 }  // namespace fwh
@@ -346,10 +386,10 @@ fw_status fw_solve_host(void* dist_host, int32_t* pred_host, int64_t n, int64_t 
   if (opt) o = *opt;
   else fw_options_default(&o);
   {
-    std::lock_guard<std::mutex> lk(g_mu);
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return FW_ERR_CUDA;
-    StreamWs& w = g_ws[{dev, s}];
+    StreamWs* wp = nullptr;
+    auto lk = lock_entry(s, &wp);
+    if (!wp) return FW_ERR_CUDA;
+    StreamWs& w = *wp;
     if (w.hbytes < bytes) {
       if (w.hd) { cudaStreamSynchronize(s); cudaFree(w.hd); cudaFree(w.hp); w.hd = w.hp = nullptr; }
       if (cudaMalloc(&w.hd, bytes) != cudaSuccess || cudaMalloc(&w.hp, bytes) != cudaSuccess) {
@@ -400,6 +440,7 @@ fw_status fw_release_workspace(void) {
   for (auto it = g_ws.begin(); it != g_ws.end();) {
     if (it->first.first == dev) {
       StreamWs& w = it->second;
+      { std::lock_guard<std::mutex> wait_for_user(w.mu); }  // no other thread is inside this entry
       if (w.base) cudaFree(w.base);
       if (w.hd) cudaFree(w.hd);
       if (w.hp) cudaFree(w.hp);

@@ -215,14 +215,9 @@ fw_status fw_backward_strided(const float* grad_dist, const float* dist, const i
   float* E = reinterpret_cast<float*>(fwh::backward_scratch(s, (size_t)(batch * st) * 4));
   if (!E) return FW_ERR_NOMEM;
   const size_t s1 = tree_smem(n), s2 = scatter_smem(n);
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_bwd_tree, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)tree_smem(kMaxN));
-    cudaFuncSetAttribute(k_bwd_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)scatter_smem(kMaxN));
-    attr = true;
-  }
+  if (fwh::kernel_setup(reinterpret_cast<const void*>(k_bwd_tree), tree_smem(kMaxN), kBT) < 1 ||
+      fwh::kernel_setup(reinterpret_cast<const void*>(k_bwd_scatter), scatter_smem(kMaxN), kBT) < 1)
+    return FW_ERR_CUDA;
   k_bwd_tree<<<(unsigned)(n * batch), kBT, s1, s>>>(grad_dist, dist, pred, E, n, ld, st);
   if (cudaGetLastError() != cudaSuccess) return FW_ERR_CUDA;
   k_bwd_scatter<<<(unsigned)(n * batch), kBT, s2, s>>>(E, pred, grad_w, n, ld, st);

@@ -279,14 +279,8 @@ fw_status plan_build(fw_batched_plan* p) {
 
   const size_t smem = fwk::WsLayout<128, T>::bytes();
   auto kern = fwk::k_batched_ws<T>;
-  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-      cudaSuccess)
-    return FW_ERR_CUDA;
-  int occ = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, fwk::kWsThreads, smem) !=
-          cudaSuccess ||
-      occ < 1)
-    return FW_ERR_CUDA;
+  const int occ = kernel_setup(reinterpret_cast<const void*>(kern), smem, fwk::kWsThreads);
+  if (occ < 1) return FW_ERR_CUDA;
   int64_t grid = (int64_t)occ * num_sms();
   if (p->opt.grid > 0 && p->opt.grid < grid) grid = p->opt.grid;
   if (grid > p->ntasks) grid = p->ntasks;

@@ -163,6 +163,12 @@ cudaError_t launch_solve_f32(float* D, int32_t* P, int64_t n, int64_t ld, const 
 
 int num_sms();
 
+// Dynamic shared-memory opt-in (smem bytes) and the number of co-resident CTAs
+// of `threads` threads per SM for kernel `fn` on the CURRENT device.  The
+// opt-in belongs to a device's context, so it is applied once per (device,
+// kernel) under a lock and cached there.  Returns <= 0 on failure.
+int kernel_setup(const void* fn, size_t smem, int threads);
+
 // Tensor map of a row-major n x n matrix of 32-bit elements with leading
 // dimension ld (elements), read in box x box tiles (2-D TMA).  False when the
 // driver offers no encoder or rejects the layout; callers then copy by rows.

@@ -35,7 +35,10 @@ static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 // Host-side cache of the device address of g_scratch, one per device.  Host
 // code must never pass `g_scratch` itself to a kernel: on the host that name is
-// only a stand-in for the symbol, not a device address.
+// only a stand-in for the symbol, not a device address.  The address is looked
+// up once per device and kept for the life of the process; after a
+// cudaDeviceReset the library's module is loaded again and the kept address is
+// stale, so calls after a device reset are not supported.
 void* g_scratch_addr[kMaxDevices] = {};
 std::mutex g_setup_mu;
 
@@ -159,10 +162,12 @@ extern "C" fw_status fw_solve_noalloc(void* dist, int32_t* pred, int64_t n, int6
                  : run<float, 64>(reinterpret_cast<float*>(dist), pred, n, ld, base, sms, s);
   }
   if (e != cudaSuccess) return FW_ERR_CUDA;
-  // synchronous: wait for this solve, then read its status word
-  if (cudaStreamSynchronize(s) != cudaSuccess) return FW_ERR_CUDA;
+  // synchronous: the status word comes back on the caller's stream, behind
+  // the solve, and only that stream is waited for (no device-wide sync)
   int st = 0;
-  if (cudaMemcpy(&st, base, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return FW_ERR_CUDA;
+  if (cudaMemcpyAsync(&st, base, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return FW_ERR_CUDA;
   if (st & fwk::kStTimeout) return FW_ERR_TIMEOUT;
   if (st & fwk::kStNegCycle) return FW_ERR_NEG_CYCLE;
   return FW_OK;

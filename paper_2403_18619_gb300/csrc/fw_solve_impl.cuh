@@ -69,13 +69,10 @@ cudaError_t launch_bs(T* D, int32_t* P, int64_t n, int64_t ld, const fwh::SolveW
   }
   if (cfg.ev_start) cudaEventRecord(cfg.ev_start, s);
   if (cfg.driver == 2) {
-    static bool attr_done = false;
-    if (!attr_done) {
-      cudaFuncSetAttribute(k_phase_pivot<T, BS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      cudaFuncSetAttribute(k_phase_panel<T, BS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      cudaFuncSetAttribute(k_phase_rest<T, BS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      attr_done = true;
-    }
+    if (fwh::kernel_setup(reinterpret_cast<const void*>(k_phase_pivot<T, BS>), smem, kThreads) < 1 ||
+        fwh::kernel_setup(reinterpret_cast<const void*>(k_phase_panel<T, BS>), smem, kThreads) < 1 ||
+        fwh::kernel_setup(reinterpret_cast<const void*>(k_phase_rest<T, BS>), smem, kThreads) < 1)
+      return cudaErrorInvalidConfiguration;
     for (int r = 0; r < R; ++r) {
       k_phase_pivot<T, BS><<<1, kThreads, smem, s>>>(a, r);
       if (R > 1) {
@@ -87,13 +84,8 @@ cudaError_t launch_bs(T* D, int32_t* P, int64_t n, int64_t ld, const fwh::SolveW
   } else {
     auto kern = k_persistent_ws<T, BS>;
     const size_t wsmem = WsLayout<BS, T>::bytes();
-    static int occ = -1;
-    if (occ < 0) {
-      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsmem);
-      int o = 0;
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, kWsThreads, wsmem);
-      occ = o > 0 ? o : 1;
-    }
+    const int occ = fwh::kernel_setup(reinterpret_cast<const void*>(kern), wsmem, kWsThreads);
+    if (occ < 1) return cudaErrorInvalidConfiguration;
     int64_t grid = cfg.grid > 0 ? cfg.grid : (int64_t)occ * fwh::num_sms();
     if (grid > (int64_t)occ * fwh::num_sms()) grid = (int64_t)occ * fwh::num_sms();
     const int64_t total = (int64_t)R * R * R;

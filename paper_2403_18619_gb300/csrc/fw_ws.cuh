@@ -76,13 +76,20 @@ struct WsBars {
 };
 
 // Bounded wait on an mbarrier phase; false (and the timeout status) on expiry.
+// With poll_abort it also gives up, without recording anything, once another
+// CTA has raised the abort flag, so that one failure does not make every
+// pending wait of every CTA run out its own limit in turn.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, int* status,
-                                          int* abort_flag, int64_t timeout_ns) {
+                                          int* abort_flag, int64_t timeout_ns,
+                                          bool poll_abort = true) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = globaltimer();
   for (int64_t it = 0; it < ((int64_t)1 << 26); ++it) {
     if (mbar_try_wait_sleep(bar, parity, 20000u)) return true;
-    if ((it & 15) == 15 && globaltimer() - t0 > (uint64_t)timeout_ns) break;
+    if ((it & 15) == 15) {
+      if (poll_abort && ld_relaxed(abort_flag)) return false;
+      if (globaltimer() - t0 > (uint64_t)timeout_ns) break;
+    }
   }
   atomicOr(status, kStTimeout);
   atomicExch(abort_flag, 1);
@@ -107,8 +114,14 @@ struct TileCtx {
 };
 
 // Counters of the shared-memory pipelines (each side keeps its own copy).
+// The producer also records, per full barrier, 1 + the last phase it armed
+// with a copy (0: none), and stops arming once a wait has given up: arming a
+// phase whose predecessor has not completed would add its bytes to the wrong
+// phase.
 struct PipeCnt {
   unsigned d = 0, chunk = 0, p = 0;
+  unsigned d_armed = 0, p_armed = 0, chunk_armed[2] = {0, 0};
+  bool stop = false;
 };
 
 // ------------------------------------------------------------ compute side ----
@@ -532,19 +545,30 @@ __device__ void issue_operands(const Args<T>& a, const fwh::Task& k, bool fast, 
     // are masked by the compute warps); a single instruction keeps the
     // producer's issue slots, shared with two compute warps, free
     if (lane == 0) {
-      mbar_wait(&wb->d_empty, (pc.d & 1) ^ 1, a.status, a.abort_flag, a.timeout_ns);
-      mbar_expect_tx(&wb->d_full, (unsigned)(BS * BS * sizeof(T)));
-      tma_load_2d(dbuf, a.tmapD, (int)col0, (int)row0, &wb->d_full);
+      if (!pc.stop && mbar_wait(&wb->d_empty, (pc.d & 1) ^ 1, a.status, a.abort_flag, a.timeout_ns)) {
+        mbar_expect_tx(&wb->d_full, (unsigned)(BS * BS * sizeof(T)));
+        tma_load_2d(dbuf, a.tmapD, (int)col0, (int)row0, &wb->d_full);
+        pc.d_armed = pc.d + 1;
+      } else {
+        pc.stop = true;
+      }
     }
   } else {
+    bool ok = false;
     if (lane == 0) {
-      mbar_wait(&wb->d_empty, (pc.d & 1) ^ 1, a.status, a.abort_flag, a.timeout_ns);
-      mbar_expect_tx(&wb->d_full, rowbytes * (unsigned)nrows);
+      ok = !pc.stop && mbar_wait(&wb->d_empty, (pc.d & 1) ^ 1, a.status, a.abort_flag, a.timeout_ns);
+      if (ok) {
+        mbar_expect_tx(&wb->d_full, rowbytes * (unsigned)nrows);
+        pc.d_armed = pc.d + 1;
+      } else {
+        pc.stop = true;
+      }
     }
-    __syncwarp();
-    for (int rr = lane; rr < nrows; rr += 32)
-      bulk_g2s(dbuf + (size_t)rr * BS * sizeof(T), a.D + (row0 + rr) * a.ld + col0, rowbytes,
-               &wb->d_full);
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    if (ok)
+      for (int rr = lane; rr < nrows; rr += 32)
+        bulk_g2s(dbuf + (size_t)rr * BS * sizeof(T), a.D + (row0 + rr) * a.ld + col0, rowbytes,
+                 &wb->d_full);
   }
   ++pc.d;
   // operand chunks
@@ -557,22 +581,30 @@ __device__ void issue_operands(const Args<T>& a, const fwh::Task& k, bool fast, 
   for (int c = 0; c < C::NC; ++c) {
     if (lane == 0) {
       const unsigned st = pc.chunk & 1;
-      mbar_wait(&wb->chunk_empty[st], ((pc.chunk >> 1) & 1) ^ 1, a.status, a.abort_flag,
-                a.timeout_ns);
-      mbar_expect_tx(&wb->chunk_full[st], 2 * (unsigned)C::kChunkBytes);
-      unsigned char* dst = smem + L::ring_off() + st * L::kStage;
-      bulk_g2s(dst, srcA + c * C::kChunkBytes, (unsigned)C::kChunkBytes, &wb->chunk_full[st]);
-      bulk_g2s(dst + C::kChunkBytes, srcB + c * C::kChunkBytes, (unsigned)C::kChunkBytes,
-               &wb->chunk_full[st]);
+      if (!pc.stop && mbar_wait(&wb->chunk_empty[st], ((pc.chunk >> 1) & 1) ^ 1, a.status,
+                                a.abort_flag, a.timeout_ns)) {
+        mbar_expect_tx(&wb->chunk_full[st], 2 * (unsigned)C::kChunkBytes);
+        unsigned char* dst = smem + L::ring_off() + st * L::kStage;
+        bulk_g2s(dst, srcA + c * C::kChunkBytes, (unsigned)C::kChunkBytes, &wb->chunk_full[st]);
+        bulk_g2s(dst + C::kChunkBytes, srcB + c * C::kChunkBytes, (unsigned)C::kChunkBytes,
+                 &wb->chunk_full[st]);
+        pc.chunk_armed[st] = pc.chunk + 1;
+      } else {
+        pc.stop = true;
+      }
     }
     ++pc.chunk;
   }
   // predecessor tile of the row panel snapshot (fp32; int32 records "via" codes)
   if (!ViaPred<T>::kOn && a.P) {
     if (lane == 0) {
-      mbar_wait(&wb->p_empty, (pc.p & 1) ^ 1, a.status, a.abort_flag, a.timeout_ns);
-      mbar_expect_tx(&wb->p_full, (unsigned)C::kTile);
-      bulk_g2s(smem + L::p_off(), a.rowP + toffB, (unsigned)C::kTile, &wb->p_full);
+      if (!pc.stop && mbar_wait(&wb->p_empty, (pc.p & 1) ^ 1, a.status, a.abort_flag, a.timeout_ns)) {
+        mbar_expect_tx(&wb->p_full, (unsigned)C::kTile);
+        bulk_g2s(smem + L::p_off(), a.rowP + toffB, (unsigned)C::kTile, &wb->p_full);
+        pc.p_armed = pc.p + 1;
+      } else {
+        pc.stop = true;
+      }
     }
     ++pc.p;
   }
@@ -747,14 +779,19 @@ __device__ void ws_engine(const Src& src, unsigned char* smem, WsBars& wb, CtaSc
       if (k.type != 3) fence_proxy_async();
       __syncwarp();
     }
-    // leave no bulk copy in flight: wait (bounded) for the last phase armed on
-    // every full barrier
+    // leave no bulk copy in flight: wait (bounded, whatever the abort flag
+    // says) for the last phase armed with a copy on every full barrier
     if (lane == 0) {
-      if (pc.d) mbar_wait(&wb.d_full, (pc.d - 1) & 1, src.status, src.abort_flag, src.timeout_ns);
-      if (pc.p) mbar_wait(&wb.p_full, (pc.p - 1) & 1, src.status, src.abort_flag, src.timeout_ns);
-      for (unsigned c = pc.chunk >= 2 ? pc.chunk - 2 : 0; c < pc.chunk; ++c)
-        mbar_wait(&wb.chunk_full[c & 1], (c >> 1) & 1, src.status, src.abort_flag,
-                  src.timeout_ns);
+      if (pc.d_armed)
+        mbar_wait(&wb.d_full, (pc.d_armed - 1) & 1, src.status, src.abort_flag, src.timeout_ns,
+                  false);
+      if (pc.p_armed)
+        mbar_wait(&wb.p_full, (pc.p_armed - 1) & 1, src.status, src.abort_flag, src.timeout_ns,
+                  false);
+      for (int st = 0; st < 2; ++st)
+        if (pc.chunk_armed[st])
+          mbar_wait(&wb.chunk_full[st], ((pc.chunk_armed[st] - 1) >> 1) & 1, src.status,
+                    src.abort_flag, src.timeout_ns, false);
     }
     return;
   }

@@ -135,3 +135,45 @@ def gpu_solve_dist_only(W: np.ndarray, *, bs=0, driver=0, packed=1, extra_ld=0):
     if ld > n:
         assert (Dh[:, n:] == canary).all(), "dist padding was written"
     return Dh[:, :n].copy()
+
+
+def check_pred_tight_int(W, Do, Pg, Po):
+    """Predecessors against the full int64 oracle: equal to the oracle's last
+    hop, or else another last hop u that is tight (an edge u -> j with
+    D[i][u] + W[u][j] == D[i][j]).  A second tight last hop means a second
+    shortest path, so on every pair with a unique shortest path the two agree,
+    and elsewhere the GPU's last hop realises the distance.  Returns the number
+    of pairs where they differ."""
+    n = W.shape[0]
+    i, j = np.nonzero(Pg != Po)
+    if len(i) == 0:
+        return 0
+    u = Pg[i, j].astype(np.int64)
+    assert ((u >= 0) & (u < n) & (u != j)).all(), "pred out of range where it differs"
+    w = W[u, j].astype(np.int64)
+    assert (w < INF).all(), "pred is not an in-neighbour where it differs"
+    bad = Do[i, u] + w != Do[i, j]
+    assert not bad.any(), "pred not tight at %d pairs, first (%d, %d)" % (
+        bad.sum(), i[bad][0], j[bad][0])
+    return len(i)
+
+
+def check_pred_near_tight_f32(W, Do, Pg, Po, tol):
+    """fp32 predecessors against the full fp64 oracle: equal to the oracle's
+    last hop, or else another last hop u whose path is within 2 * tol of the
+    shortest distance in fp64 (D[i][u] + W[u][j] <= D[i][j] + 2 tol[i][j]).
+    The oracle's margin of such a pair is then at most 2 tol, so on every
+    margin-safe pair the two agree.  Returns the number of differing pairs."""
+    n = W.shape[0]
+    i, j = np.nonzero(Pg != Po)
+    if len(i) == 0:
+        return 0
+    u = Pg[i, j].astype(np.int64)
+    assert ((u >= 0) & (u < n) & (u != j)).all(), "pred out of range where it differs"
+    w = W[u, j].astype(np.float64)
+    assert np.isfinite(w).all(), "pred is not an in-neighbour where it differs"
+    gap = Do[i, u] + w - Do[i, j]
+    bad = gap > 2 * tol[i, j]
+    assert not bad.any(), "pred not near-tight at %d pairs, first (%d, %d) gap %g tol %g" % (
+        bad.sum(), i[bad][0], j[bad][0], gap[bad][0], tol[i[bad][0], j[bad][0]])
+    return len(i)

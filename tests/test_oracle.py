@@ -233,6 +233,17 @@ def test_vs_scipy_float(n, p, seed):
     mg = oracle.lasthop_margin_f64(W, D, P)
     safe = reach & (mg > 1e-9 * np.maximum(D, 1))
     np.testing.assert_array_equal(P[safe], pred[safe])
+    # the Dijkstra oracle's predecessors: scipy's on the same margin-safe pairs,
+    # and a tight last hop (an edge whose use realises the distance) everywhere
+    np.testing.assert_array_equal(Pd[safe], pred[safe])
+    off = reach & ~np.eye(n, dtype=bool)
+    i, j = np.nonzero(off)
+    u = Pd[i, j]
+    assert (u >= 0).all() and (u != j).all()
+    Wd = W.astype(np.float64)
+    assert np.isfinite(Wd[u, j]).all()
+    np.testing.assert_allclose(Dd[i, u] + Wd[u, j], Dd[i, j], rtol=1e-12, atol=0)
+    assert (Pd[~off] == -1).all()
     assert safe.sum() > n
 
 
@@ -294,6 +305,43 @@ def test_hops_and_margins():
     assert m[0, 2] == 2
     # 0 -> 1 has no other in-neighbour than 0 except 3 (D03 + W31? no edge 3->1) -> no alternative
     assert m[0, 1] == np.iinfo(np.int64).max
+
+
+def test_lasthop_margin_f64_hand_values():
+    """The fp64 margin on the hand-worked graph read as fp32 weights (every
+    weight and sum is exact in binary floating point), worked out by hand:
+      0 -> 2: last hop 1 (d 5); the other in-neighbour of 2 is 0 (direct 7): 7 - 5 = 2
+      0 -> 1: the only in-neighbour of 1 is 0, its last hop: no alternative (+inf)
+      2 -> 4: last hop 3 (d 10 = 1 + 9); the other in-neighbour of 4 is 1 (d(2,1) 7 + 6 = 13): 3
+      4 -> 0: last hop 3 (d 6); 0 has no other in-neighbour: +inf
+      diagonal and unreachable entries: -1."""
+    W, D, P = load_hand5()
+    Wf = np.where(W >= INF, np.float32(np.inf), W.astype(np.float32)).astype(np.float32)
+    Df, Pf = oracle.fw_f64(Wf)
+    np.testing.assert_array_equal(Df, D.astype(np.float64))
+    np.testing.assert_array_equal(Pf, P)
+    m = oracle.lasthop_margin_f64(Wf, Df, Pf)
+    assert m[0, 2] == 2.0
+    assert np.isinf(m[0, 1]) and m[0, 1] > 0
+    assert m[2, 4] == 3.0
+    assert np.isinf(m[4, 0]) and m[4, 0] > 0
+    assert (np.diag(m) == -1.0).all()
+    # the integer margin agrees wherever both are finite
+    mi = oracle.lasthop_margin_i64(W, D, P)
+    fin = np.isfinite(m) & (mi != np.iinfo(np.int64).max)
+    np.testing.assert_array_equal(m[fin], mi[fin].astype(np.float64))
+    # a planted alternative: an edge 3 -> 2 of weight 6 gives 0 -> 2 a second
+    # last hop at d(0,3) + 6 = 12, which does not lower the margin below 2
+    W2 = Wf.copy(); W2[3, 2] = 6.0
+    D2, P2 = oracle.fw_f64(W2)
+    assert oracle.lasthop_margin_f64(W2, D2, P2)[0, 2] == 2.0
+    # weight 0.5 on 3 -> 2 makes 0 -> 1 -> 2 -> 3 -> 2 irrelevant but 4 -> 3 -> 2
+    # (2 + 0.5 = 2.5) beats 4 -> 3 -> 0 -> 1 -> 2 (11): last hop 3, margin to the
+    # old last hop 1 (d(4,1) 8 + 3 = 11) is 8.5
+    W3 = Wf.copy(); W3[3, 2] = 0.5
+    D3, P3 = oracle.fw_f64(W3)
+    assert D3[4, 2] == 2.5 and P3[4, 2] == 3
+    assert oracle.lasthop_margin_f64(W3, D3, P3)[4, 2] == 8.5
 
 
 # ---------------------------------------------------------------- gradient ---

@@ -69,3 +69,38 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     fake = 0x100000
     assert lib.fw_solve_noalloc(fake, fake + (1 << 20), 4097, 4100, fw.FW_I32, None) == 6
     assert lib.fw_solve_noalloc(None, fake, 64, 64, fw.FW_I32, None) == 1
+
+
+def test_noalloc_largest_size_and_status():
+    """n = 4096, the largest size the static array covers (BS 64, R = 64, the
+    largest carve): same result as fw_solve and the exhaustive certificate.
+    Then a graph with a negative cycle, whose status must come back from the
+    call as FW_ERR_NEG_CYCLE, and a normal call after it."""
+    import torch
+    import paper_2403_18619_gb300 as fw
+    n = 4096
+    W = graphgen.dense_graph_i32(n, seed=45, p=0.5, lo=1, hi=1000)
+    Dr, Pr = _pair(W)
+    fw.fw_solve(Dr[:, :n], Pr[:, :n])
+    fw.fw_sync_status()
+    D, P = _pair(W)
+    fw.fw_solve_noalloc(D[:, :n], P[:, :n])
+    assert torch.equal(D[:, :n], Dr[:, :n])
+    assert torch.equal(P[:, :n], Pr[:, :n])
+    Wd = torch.from_numpy(W).cuda()
+    bad = fw.fw_verify_certificate(Wd, D[:, :n].contiguous(), P[:, :n].contiguous())
+    assert bad.sum() == 0, bad.tolist()
+
+    m = 64
+    Wn = graphgen.dense_graph_i32(m, seed=2, p=0.3, lo=1, hi=9)
+    Wn[5, 6], Wn[6, 7], Wn[7, 5] = 1, 1, -10
+    Dn, Pn = _pair(Wn)
+    with pytest.raises(fw.FWError) as e:
+        fw.fw_solve_noalloc(Dn[:, :m], Pn[:, :m])
+    assert e.value.code == 4
+    # the next call starts from a cleared status word
+    Wg = graphgen.dense_graph_i32(200, seed=46, p=0.5, lo=1, hi=50)
+    Dg, Pg = _pair(Wg)
+    fw.fw_solve_noalloc(Dg[:, :200], Pg[:, :200])
+    Do, _ = oracle.fw_i64(Wg)
+    np.testing.assert_array_equal(Dg[:, :200].cpu().numpy().astype(np.int64), Do)
