@@ -19,7 +19,11 @@ Counter layout for element (i, j) of an n-vertex graph and stream s in {0, 1}:
 * int32 weight         =  lo + h(.., 0) mod (hi - lo + 1)
 * fp32 weight in (0,1] =  ((h(.., 0) >> 40) + 1) * 2**-24
 * fp32 weight in [1,2) =  1 + (h(.., 0) >> 40) * 2**-24
-* D[i][i] = 0; a missing edge is INF (2**29 for int32, +inf for fp32).
+* fp64 weight in (0,1] =  ((h(.., 0) >> 11) + 1) * 2**-53
+* fp64 weight in [1,2) =  1 + (h(.., 0) >> 12) * 2**-52
+* int64 weight         =  lo + h(.., 0) mod (hi - lo + 1)
+* D[i][i] = 0; a missing edge is INF (2**29 for int32, 2**61 for int64, +inf
+  for the floating types).
 
 The paper's own inputs are synthetic dense distance matrices with a share of
 null entries (Sec. 4.1); no public dataset is involved.
@@ -32,6 +36,7 @@ GAMMA = np.uint64(0x9E3779B97F4A7C15)
 _M1 = np.uint64(0xBF58476D1CE4E5B9)
 _M2 = np.uint64(0x94D049BB133111EB)
 INF_I32 = 1 << 29
+INF_I64 = 1 << 61
 
 KIND_UNIT = 0      # fp32 weights in (0, 1]
 KIND_ONE_TWO = 1   # fp32 weights in [1, 2)
@@ -101,6 +106,45 @@ def dense_graph_f32(n: int, seed: int, p: float, kind: int = KIND_UNIT,
     return out
 
 
+def dense_graph_i64(n: int, seed: int, p: float, lo: int, hi: int,
+                    inf: int = INF_I64, rows=None, chunk_rows: int = 1024) -> np.ndarray:
+    """Directed graph with int64 weights uniform in [lo, hi]; returns rows x n."""
+    rows = np.arange(n) if rows is None else np.asarray(rows)
+    out = np.empty((len(rows), n), dtype=np.int64)
+    span = np.uint64(hi - lo + 1)
+    for s in range(0, len(rows), chunk_rows):
+        rr = rows[s:s + chunk_rows]
+        h0 = splitmix64(_counters(seed, n, rr, 0))
+        w = np.int64(lo) + (h0 % span).astype(np.int64)
+        m = _edge_mask(seed, n, rr, p)
+        blk = np.where(m, w, np.int64(inf))
+        blk[np.arange(len(rr)), rr] = 0
+        out[s:s + chunk_rows] = blk
+    return out
+
+
+def dense_graph_f64(n: int, seed: int, p: float, kind: int = KIND_UNIT,
+                    rows=None, chunk_rows: int = 1024) -> np.ndarray:
+    """Directed graph with fp64 weights (full 53-bit mantissas) in (0,1]
+    (KIND_UNIT) or [1,2) (KIND_ONE_TWO)."""
+    rows = np.arange(n) if rows is None else np.asarray(rows)
+    out = np.empty((len(rows), n), dtype=np.float64)
+    for s in range(0, len(rows), chunk_rows):
+        rr = rows[s:s + chunk_rows]
+        h0 = splitmix64(_counters(seed, n, rr, 0))
+        if kind == KIND_UNIT:
+            w = ((h0 >> np.uint64(11)).astype(np.float64) + 1.0) * 2.0 ** -53
+        elif kind == KIND_ONE_TWO:
+            w = 1.0 + (h0 >> np.uint64(12)).astype(np.float64) * 2.0 ** -52
+        else:
+            raise ValueError("unknown weight kind")
+        m = _edge_mask(seed, n, rr, p)
+        blk = np.where(m, w, np.inf)
+        blk[np.arange(len(rr)), rr] = 0.0
+        out[s:s + chunk_rows] = blk
+    return out
+
+
 def batch_sizes(seed: int, batch: int, lo: int = 64, hi: int = 2048) -> np.ndarray:
     """Vertex counts of a batch, uniform in [lo, hi]: lo + h(seed, b, 0, 0) mod (hi-lo+1)."""
     b = np.arange(batch, dtype=np.uint64)
@@ -126,7 +170,10 @@ def normal_f32(shape, seed: int) -> np.ndarray:
 def adjoint_for(dist: np.ndarray, seed: int) -> np.ndarray:
     """dL/dD ~ N(0,1) on reachable off-diagonal pairs and 0 elsewhere."""
     g = normal_f32(dist.shape, seed)
-    reach = np.isfinite(dist) if dist.dtype.kind == "f" else dist < INF_I32
+    if dist.dtype.kind == "f":
+        reach = np.isfinite(dist)
+    else:
+        reach = dist < (INF_I64 if dist.dtype == np.int64 else INF_I32)
     reach = reach.copy()
     np.fill_diagonal(reach, False)
     return np.where(reach, g, np.float32(0.0)).astype(np.float32)

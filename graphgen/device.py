@@ -37,6 +37,10 @@ def _load():
                                           ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P]
         lib.graphgen_fill_f32.argtypes = [P, I64, I64, ctypes.c_uint64, ctypes.c_double,
                                           ctypes.c_int, P]
+        lib.graphgen_fill_i64.argtypes = [P, I64, I64, ctypes.c_uint64, ctypes.c_double,
+                                          I64, I64, I64, P]
+        lib.graphgen_fill_f64.argtypes = [P, I64, I64, ctypes.c_uint64, ctypes.c_double,
+                                          ctypes.c_int, P]
         _lib = lib
     return _lib
 
@@ -59,4 +63,20 @@ def fill_f32(t, seed: int, p: float, kind: int = 0, stream=None):
     rc = _load().graphgen_fill_f32(t.data_ptr(), n, ld, seed, p, kind, _stream(stream))
     if rc:
         raise RuntimeError("graphgen_fill_f32 failed (%d)" % rc)
+    return t
+
+
+def fill_i64(t, seed: int, p: float, lo: int, hi: int, inf: int = 1 << 61, stream=None):
+    n, ld = t.shape[0], t.stride(0)
+    rc = _load().graphgen_fill_i64(t.data_ptr(), n, ld, seed, p, lo, hi, inf, _stream(stream))
+    if rc:
+        raise RuntimeError("graphgen_fill_i64 failed (%d)" % rc)
+    return t
+
+
+def fill_f64(t, seed: int, p: float, kind: int = 0, stream=None):
+    n, ld = t.shape[0], t.stride(0)
+    rc = _load().graphgen_fill_f64(t.data_ptr(), n, ld, seed, p, kind, _stream(stream))
+    if rc:
+        raise RuntimeError("graphgen_fill_f64 failed (%d)" % rc)
     return t

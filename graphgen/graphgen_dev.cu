@@ -67,6 +67,45 @@ __global__ void fill_f32(float* out, int64_t n, int64_t ld, uint64_t seed, doubl
   }
 }
 
+__global__ void fill_i64(int64_t* out, int64_t n, int64_t ld, uint64_t seed, double p,
+                         int64_t lo, int64_t hi, int64_t inf) {
+  const uint64_t span = (uint64_t)(hi - lo) + 1;
+  const int64_t total = n * n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / n, j = e - i * n;
+    int64_t v;
+    if (i == j) {
+      v = 0;
+    } else if (edge_present(seed, n, i, j, p)) {
+      uint64_t h0 = splitmix64(counter(seed, n, i, j, 0));
+      v = lo + (int64_t)(h0 % span);
+    } else {
+      v = inf;
+    }
+    out[i * ld + j] = v;
+  }
+}
+
+__global__ void fill_f64(double* out, int64_t n, int64_t ld, uint64_t seed, double p,
+                         int kind) {
+  const int64_t total = n * n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / n, j = e - i * n;
+    double v;
+    if (i == j) {
+      v = 0.0;
+    } else if (edge_present(seed, n, i, j, p)) {
+      uint64_t h0 = splitmix64(counter(seed, n, i, j, 0));
+      v = kind == 0 ? ((double)(h0 >> 11) + 1.0) * 0x1p-53 : 1.0 + (double)(h0 >> 12) * 0x1p-52;
+    } else {
+      v = __longlong_as_double(0x7ff0000000000000ll);
+    }
+    out[i * ld + j] = v;
+  }
+}
+
 int grid_for(int64_t total) {
   int64_t g = (total + 255) / 256;
   if (g > 152 * 32) g = 152 * 32;
@@ -93,6 +132,22 @@ int graphgen_fill_f32(float* out, int64_t n, int64_t ld, uint64_t seed, double p
                       void* stream) {
   if (!out || n <= 0 || ld < n || (kind != 0 && kind != 1)) return 1;
   fill_f32<<<grid_for(n * n), 256, 0, (cudaStream_t)stream>>>(out, n, ld, seed, p, kind);
+  return cudaGetLastError() == cudaSuccess ? 0 : 2;
+}
+
+// int64 weights in [lo, hi] (missing edges inf).
+int graphgen_fill_i64(int64_t* out, int64_t n, int64_t ld, uint64_t seed, double p, int64_t lo,
+                      int64_t hi, int64_t inf, void* stream) {
+  if (!out || n <= 0 || ld < n || hi < lo) return 1;
+  fill_i64<<<grid_for(n * n), 256, 0, (cudaStream_t)stream>>>(out, n, ld, seed, p, lo, hi, inf);
+  return cudaGetLastError() == cudaSuccess ? 0 : 2;
+}
+
+// fp64 weights; kind 0 draws (0,1], kind 1 draws [1,2).
+int graphgen_fill_f64(double* out, int64_t n, int64_t ld, uint64_t seed, double p, int kind,
+                      void* stream) {
+  if (!out || n <= 0 || ld < n || (kind != 0 && kind != 1)) return 1;
+  fill_f64<<<grid_for(n * n), 256, 0, (cudaStream_t)stream>>>(out, n, ld, seed, p, kind);
   return cudaGetLastError() == cudaSuccess ? 0 : 2;
 }
 

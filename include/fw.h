@@ -20,7 +20,8 @@
  *   - int32 path: a missing edge is FW_INF_I32 = 2^29; weights are in
  *     [0, FW_INF_I32) and every simple path is shorter than FW_INF_I32, i.e.
  *     (n-1) * max_weight < 2^29.  Results for unreachable pairs are exactly
- *     FW_INF_I32.  fp32 path: a missing edge is +inf; no NaN.
+ *     FW_INF_I32.  int64 path: the same with FW_INF_I64 = 2^61.  fp32 and
+ *     fp64 paths: a missing edge is +inf; no NaN.
  *   - D[i][i] must be 0 on entry and weights must be >= 0; results for
  *     negative weights are undefined, except that a negative diagonal entry
  *     seen during the solve is reported as FW_ERR_NEG_CYCLE.
@@ -59,8 +60,15 @@ extern "C" {
 #endif
 
 #define FW_INF_I32 (1 << 29)
+#define FW_INF_I64 (1LL << 61)
 
-typedef enum { FW_I32 = 0, FW_F32 = 1 } fw_dtype;
+/* Element type of dist.  FW_I32 / FW_F32: the hot path (DPX packed keys for
+ * int32).  FW_I64 / FW_F64: the paper's double-precision runs (Sec. 4, float
+ * and double) and 64-bit integer weights; fw_solve, fw_solve_ex and
+ * fw_solve_host take them, with BS 32 or 64 (three 128 x 128 tiles of 8-byte
+ * elements do not fit in one SM's shared memory); the batched, backward,
+ * allocation-free and certificate entry points return FW_ERR_UNSUPPORTED. */
+typedef enum { FW_I32 = 0, FW_F32 = 1, FW_I64 = 2, FW_F64 = 3 } fw_dtype;
 
 typedef enum {
   FW_OK = 0,
@@ -125,8 +133,9 @@ const char* fw_status_string(fw_status s);
  *         for a distance-only solve (no predecessor work at all; fp32 then
  *         relaxes with an add and a min per step instead of compare+select).
  *   n     vertices, 1 <= n <= 131072.   ld  leading dimension, ld >= n, ld % 4 == 0.
- *   dtype FW_I32 or FW_F32.
- * Returns FW_OK once the work is enqueued.
+ *   dtype FW_I32, FW_F32, FW_I64 or FW_F64.
+ * Returns FW_OK once the work is enqueued; FW_ERR_UNSUPPORTED for BS = 128
+ * with a 64-bit dtype (automatic BS for them: 32 up to n = 512, else 64).
  */
 fw_status fw_solve(void* dist, int32_t* pred, int64_t n, int64_t ld, fw_dtype dtype, void* stream);
 
@@ -230,7 +239,7 @@ fw_status fw_release_workspace(void);
  * fw_peak_probe: measures the min-plus relaxation peak of this GPU at its
  * current clocks with register-resident relaxation chains on every SM (the
  * same instruction the solver's inner loop issues: __viaddmin for int32,
- * add + min for fp32).  Outputs relaxations per second, relaxations per SM
+ * add + min for fp32, fp64 and int64).  Outputs relaxations per second, relaxations per SM
  * clock cycle (clock-independent) and the average SM clock in MHz seen by the
  * probe.  Synchronous.  Not part of the paper: it provides the roofline.
  */

@@ -34,6 +34,7 @@ _lock = threading.Lock()
 _lib = None
 
 INF_I32 = 1 << 29
+INF_I64 = 1 << 61
 
 
 def build(force: bool = False) -> str:
@@ -84,11 +85,14 @@ def threads_default() -> int:
     return int(os.environ.get("ORACLE_THREADS", "0"))
 
 
-def fw_i64(W: np.ndarray, inf: int = INF_I32, threads: int | None = None):
-    """Plain FW (Fig. 1) on int32 weights in int64: returns (D int64, P int32)."""
+def fw_i64(W: np.ndarray, inf: int | None = None, threads: int | None = None):
+    """Plain FW (Fig. 1) on int32 or int64 weights in int64: returns (D int64,
+    P int32).  inf defaults to 2**29 for int32 weights and 2**61 for int64."""
     lib = _load()
     n = W.shape[0]
-    W, wp = _c(W, np.int32)
+    if inf is None:
+        inf = INF_I64 if np.asarray(W).dtype == np.int64 else INF_I32
+    W, wp = _c(W, np.int64)
     D = np.empty((n, n), np.int64)
     P = np.empty((n, n), np.int32)
     lib.oracle_fw_i64(wp, n, inf, D.ctypes.data, P.ctypes.data,
@@ -97,10 +101,10 @@ def fw_i64(W: np.ndarray, inf: int = INF_I32, threads: int | None = None):
 
 
 def fw_f64(W: np.ndarray, threads: int | None = None):
-    """Plain FW (Fig. 1) on fp32 weights in fp64: returns (D float64, P int32)."""
+    """Plain FW (Fig. 1) on fp32 or fp64 weights in fp64: returns (D float64, P int32)."""
     lib = _load()
     n = W.shape[0]
-    W, wp = _c(W, np.float32)
+    W, wp = _c(W, np.float64)
     D = np.empty((n, n), np.float64)
     P = np.empty((n, n), np.int32)
     lib.oracle_fw_f64(wp, n, D.ctypes.data, P.ctypes.data,

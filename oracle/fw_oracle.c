@@ -38,8 +38,9 @@ typedef int64_t i64;
 
 /* ---------------------------------------------------------------- FW ---- */
 
-/* Fig. 1 (Sec. 2.3), integer weights.  W: n x n int32, row-major. */
-void oracle_fw_i64(const int32_t* W, i64 n, i64 inf, i64* D, int32_t* P, int threads) {
+/* Fig. 1 (Sec. 2.3), integer weights.  W: n x n int64, row-major (int32
+   inputs are widened by the caller). */
+void oracle_fw_i64(const i64* W, i64 n, i64 inf, i64* D, int32_t* P, int threads) {
   OMP_THREADS(threads);
   for (i64 i = 0; i < n; ++i)
     for (i64 j = 0; j < n; ++j) {
@@ -67,12 +68,13 @@ void oracle_fw_i64(const int32_t* W, i64 n, i64 inf, i64* D, int32_t* P, int thr
   }
 }
 
-/* Fig. 1 (Sec. 2.3), real weights in fp64. */
-void oracle_fw_f64(const float* W, i64 n, double* D, int32_t* P, int threads) {
+/* Fig. 1 (Sec. 2.3), real weights in fp64.  W: n x n fp64 (fp32 inputs are
+   widened by the caller, which is exact). */
+void oracle_fw_f64(const double* W, i64 n, double* D, int32_t* P, int threads) {
   OMP_THREADS(threads);
   for (i64 i = 0; i < n; ++i)
     for (i64 j = 0; j < n; ++j) {
-      double w = (double)W[i * n + j];
+      double w = W[i * n + j];
       D[i * n + j] = w;
       P[i * n + j] = (i != j && !isinf(w)) ? (int32_t)i : -1;
     }

@@ -19,15 +19,16 @@ __all__ = [
     "fw_solve_noalloc", "fw_sync_status", "fw_backward", "fw_backward_strided",
     "fw_peak_probe", "fw_verify_certificate", "fw_release_workspace", "fw_solve_plan",
     "fw_queue_tasks", "fw_paths", "BatchedPlan", "fw_bs_table", "fw_autotune_bs", "padded", "solve",
-    "solve_batched", "INF_I32", "FW_I32", "FW_F32", "DRIVER_AUTO", "DRIVER_PERSISTENT",
-    "DRIVER_PHASED",
+    "solve_batched", "INF_I32", "INF_I64", "FW_I32", "FW_F32", "FW_I64", "FW_F64", "DRIVER_AUTO",
+    "DRIVER_PERSISTENT", "DRIVER_PHASED",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libfw.so")
 
 INF_I32 = 1 << 29
-FW_I32, FW_F32 = 0, 1
+INF_I64 = 1 << 61
+FW_I32, FW_F32, FW_I64, FW_F64 = 0, 1, 2, 3
 DRIVER_AUTO, DRIVER_PERSISTENT, DRIVER_PHASED = 0, 1, 2
 
 STATUS = {0: "FW_OK", 1: "FW_ERR_ARG", 2: "FW_ERR_CUDA", 3: "FW_ERR_TIMEOUT",
@@ -136,11 +137,11 @@ def _stream_ptr(stream):
 
 def _dtype_code(t) -> int:
     import torch
-    if t.dtype == torch.int32:
-        return FW_I32
-    if t.dtype == torch.float32:
-        return FW_F32
-    raise TypeError("dist must be int32 or float32, got %s" % t.dtype)
+    codes = {torch.int32: FW_I32, torch.float32: FW_F32, torch.int64: FW_I64,
+             torch.float64: FW_F64}
+    if t.dtype not in codes:
+        raise TypeError("dist must be int32, float32, int64 or float64, got %s" % t.dtype)
+    return codes[t.dtype]
 
 
 def _matrix(t, name):
@@ -201,9 +202,10 @@ def fw_solve_host(dist: np.ndarray, pred: np.ndarray, options: Options | None = 
         if dist.ndim != 2 or dist.strides[1] != dist.itemsize:
             raise ValueError("dist must be a 2-D array with unit column stride")
         n, ld = dist.shape[0], dist.strides[0] // dist.itemsize
-        code = FW_I32 if dist.dtype == np.int32 else FW_F32 if dist.dtype == np.float32 else None
+        code = {np.dtype(np.int32): FW_I32, np.dtype(np.float32): FW_F32,
+                np.dtype(np.int64): FW_I64, np.dtype(np.float64): FW_F64}.get(dist.dtype)
         if code is None:
-            raise TypeError("dist must be int32 or float32")
+            raise TypeError("dist must be int32, float32, int64 or float64")
         dptr = dist.ctypes.data
         pptr = pred.ctypes.data if pred is not None else None
     o = ctypes.byref(options) if options is not None else None

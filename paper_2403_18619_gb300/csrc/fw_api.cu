@@ -62,16 +62,18 @@ EncodeTiledFn encode_fn() {
 }
 }  // namespace
 
-bool encode_tile_map(CUtensorMap* map, const void* base, int64_t n, int64_t ld, int box, bool f32) {
+bool encode_tile_map(CUtensorMap* map, const void* base, int64_t n, int64_t ld, int box,
+                     CUtensorMapDataType dt, int esize) {
   EncodeTiledFn fn = encode_fn();
-  if (!fn || n <= 0 || box <= 0 || box > 256) return false;
-  if ((reinterpret_cast<uintptr_t>(base) & 15) || ((ld * 4) & 15)) return false;
+  if (!fn || n <= 0 || box <= 0 || box > 256 || (esize != 4 && esize != 8)) return false;
+  if ((reinterpret_cast<uintptr_t>(base) & 15) || ((ld * esize) & 15)) return false;
+  if (((int64_t)box * esize) & 15) return false;
   const cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)n};
-  const cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * esize};
   const cuuint32_t boxd[2] = {(cuuint32_t)box, (cuuint32_t)box};
   const cuuint32_t estr[2] = {1, 1};
   // elements outside [0, n) read as zero; the kernels mask them
-  return fn(map, f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_INT32, 2,
+  return fn(map, dt, 2,
             const_cast<void*>(base), dims, strides, boxd, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
@@ -111,18 +113,21 @@ int kernel_setup(const void* fn, size_t smem, int threads) {
   return occ;
 }
 
-size_t solve_ws_bytes(int R, int BS) {
+size_t solve_ws_bytes(int R, int BS, int esize) {
   const size_t t = (size_t)BS * BS;
+  const size_t keys = esize == 4 ? 2 : 0;  // packed-key snapshots (32-bit elements only)
   size_t b = 0;
   b += up(((size_t)R * R + 2 * (size_t)R) * 4 + 4 * 4 + 4);  // ver + done + ctr + abort
-  b += up((size_t)(R + 2) * 4);            // stage offsets
-  b += up(2 * t * 4) * 2;                  // piv, pivP
-  b += up(2 * (size_t)R * t * 4) * 5;      // colK, colR, rowK, rowR, rowP
-  b += up(2 * (size_t)R * 4) * 2;          // colB, rowB
+  b += up((size_t)(R + 2) * 4);              // stage offsets
+  b += up(2 * t * esize) + up(2 * t * 4);    // piv, pivP
+  b += up(2 * (size_t)R * t * 4) * keys;     // colK, rowK
+  b += up(2 * (size_t)R * t * esize) * 2;    // colR, rowR
+  b += up(2 * (size_t)R * t * 4);            // rowP
+  b += up(2 * (size_t)R * 4) * 2;            // colB, rowB
   return b + kAlign;
 }
 
-SolveWs carve_solve_ws(void* base, int R, int BS) {
+SolveWs carve_solve_ws(void* base, int R, int BS, int esize) {
   SolveWs w;
   char* p = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(base) + kAlign - 1) / kAlign * kAlign);
   const size_t t = (size_t)BS * BS;
@@ -133,12 +138,14 @@ SolveWs carve_solve_ws(void* base, int R, int BS) {
   w.flags_bytes = ((size_t)R * R + 2 * (size_t)R) * 4 + 4 * 4 + 4;
   p += up(w.flags_bytes);
   w.stage_off = reinterpret_cast<unsigned*>(p);  p += up((size_t)(R + 2) * 4);
-  w.piv = p;                                     p += up(2 * t * 4);
+  w.piv = p;                                     p += up(2 * t * esize);
   w.pivP = reinterpret_cast<int32_t*>(p);        p += up(2 * t * 4);
-  w.colK = reinterpret_cast<uint32_t*>(p);       p += up(2 * (size_t)R * t * 4);
-  w.colR = p;                                    p += up(2 * (size_t)R * t * 4);
-  w.rowK = reinterpret_cast<uint32_t*>(p);       p += up(2 * (size_t)R * t * 4);
-  w.rowR = p;                                    p += up(2 * (size_t)R * t * 4);
+  if (esize == 4) {
+    w.colK = reinterpret_cast<uint32_t*>(p);     p += up(2 * (size_t)R * t * 4);
+    w.rowK = reinterpret_cast<uint32_t*>(p);     p += up(2 * (size_t)R * t * 4);
+  }
+  w.colR = p;                                    p += up(2 * (size_t)R * t * esize);
+  w.rowR = p;                                    p += up(2 * (size_t)R * t * esize);
   w.rowP = reinterpret_cast<int32_t*>(p);        p += up(2 * (size_t)R * t * 4);
   w.colB = reinterpret_cast<int32_t*>(p);        p += up(2 * (size_t)R * 4);
   w.rowB = reinterpret_cast<int32_t*>(p);        p += up(2 * (size_t)R * 4);
@@ -151,10 +158,15 @@ SolveWs carve_solve_ws(void* base, int R, int BS) {
 // whose pivot -> panel chain is longer; measured on GB300 (int32, persistent
 // driver): n = 2048 BS 64 1.27 ms vs BS 128 2.16 ms; n = 4096 BS 64 7.70 ms vs
 // BS 128 5.91 ms.  The two costs cross near n = 3072.
-int pick_bs(int64_t n) {
+int pick_bs(int64_t n, fw_dtype dtype = FW_I32) {
   if (n <= 512) return 32;
-  if (n <= 3072) return 64;
+  if (n <= 3072 || dtype == FW_I64 || dtype == FW_F64) return 64;
   return 128;
+}
+
+int dtype_size(fw_dtype dtype) { return (dtype == FW_I64 || dtype == FW_F64) ? 8 : 4; }
+bool dtype_valid(fw_dtype dtype) {
+  return dtype == FW_I32 || dtype == FW_F32 || dtype == FW_I64 || dtype == FW_F64;
 }
 
 // The workspace entry of (current device, stream), created if missing, locked
@@ -219,7 +231,9 @@ fw_status check_options(const fw_options& o) {
 
 fw_status solve_device(void* dist, int32_t* pred, int64_t n, int64_t ld, fw_dtype dtype,
                        const fw_options& o, cudaStream_t s) {
-  const int BS = o.bs ? o.bs : pick_bs(n);
+  const int esize = dtype_size(dtype);
+  const int BS = o.bs ? o.bs : pick_bs(n, dtype);
+  if (esize == 8 && BS > 64) return FW_ERR_UNSUPPORTED;
   const int64_t R64 = (n + BS - 1) / BS;
   if (R64 > 1024) return FW_ERR_UNSUPPORTED;
   const int R = (int)R64;
@@ -229,9 +243,9 @@ fw_status solve_device(void* dist, int32_t* pred, int64_t n, int64_t ld, fw_dtyp
   StreamWs* w = nullptr;
   auto lk = lock_entry(s, &w);
   if (!w) return FW_ERR_CUDA;
-  fw_status st = get_ws(*w, s, solve_ws_bytes(R, BS));
+  fw_status st = get_ws(*w, s, solve_ws_bytes(R, BS, esize));
   if (st != FW_OK) return st;
-  SolveWs ws = carve_solve_ws(w->base, R, BS);
+  SolveWs ws = carve_solve_ws(w->base, R, BS, esize);
   ws.status = w->status;
   if (w->cached_R != R || w->cached_BS != BS || w->cached_look != look) {
     std::vector<unsigned> off(R + 2);
@@ -257,9 +271,13 @@ fw_status solve_device(void* dist, int32_t* pred, int64_t n, int64_t ld, fw_dtyp
   cfg.trace_cap = o.trace_cap;
   cfg.trace_stride = o.trace_stride;
   cfg.tile_tma = o.tile_tma != 0;
-  cudaError_t e = dtype == FW_I32
-                      ? launch_solve_i32(reinterpret_cast<int32_t*>(dist), pred, n, ld, ws, cfg, s)
-                      : launch_solve_f32(reinterpret_cast<float*>(dist), pred, n, ld, ws, cfg, s);
+  cudaError_t e = cudaErrorInvalidValue;
+  switch (dtype) {
+    case FW_I32: e = launch_solve_i32(reinterpret_cast<int32_t*>(dist), pred, n, ld, ws, cfg, s); break;
+    case FW_F32: e = launch_solve_f32(reinterpret_cast<float*>(dist), pred, n, ld, ws, cfg, s); break;
+    case FW_I64: e = launch_solve_i64(reinterpret_cast<int64_t*>(dist), pred, n, ld, ws, cfg, s); break;
+    case FW_F64: e = launch_solve_f64(reinterpret_cast<double*>(dist), pred, n, ld, ws, cfg, s); break;
+  }
   return e == cudaSuccess ? FW_OK : FW_ERR_CUDA;
 }
 
@@ -348,7 +366,7 @@ fw_status fw_solve_ex(void* dist, int32_t* pred, int64_t n, int64_t ld, fw_dtype
   if (opt) o = *opt;
   fw_status st = check_matrix_args(dist, pred, n, ld);
   if (st != FW_OK) return st;
-  if (dtype != FW_I32 && dtype != FW_F32) return FW_ERR_ARG;
+  if (!dtype_valid(dtype)) return FW_ERR_ARG;
   if ((st = check_options(o)) != FW_OK) return st;
   return solve_device(dist, pred, n, ld, dtype, o, reinterpret_cast<cudaStream_t>(stream));
 }
@@ -375,9 +393,10 @@ fw_status fw_solve_host(void* dist_host, int32_t* pred_host, int64_t n, int64_t 
                         fw_dtype dtype, const fw_options* opt, void* stream) {
   if (!dist_host) return FW_ERR_ARG;
   if (n <= 0 || n > 131072 || ld < n || (ld % 4) != 0) return FW_ERR_ARG;
-  if (dtype != FW_I32 && dtype != FW_F32) return FW_ERR_ARG;
+  if (!dtype_valid(dtype)) return FW_ERR_ARG;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  const size_t bytes = (size_t)n * ld * 4;
+  const size_t bytes = (size_t)n * ld * dtype_size(dtype);  // dist
+  const size_t pbytes = (size_t)n * ld * 4;                 // pred
   void* dd = nullptr;
   void* dp = nullptr;
   cudaStream_t side = nullptr;
@@ -426,7 +445,7 @@ fw_status fw_solve_host(void* dist_host, int32_t* pred_host, int64_t n, int64_t 
       cudaMemcpyAsync(dist_host, dd, bytes, cudaMemcpyDeviceToHost, side) != cudaSuccess ||
       cudaEventRecord(ev_side, side) != cudaSuccess ||
       (pred_host &&
-       cudaMemcpyAsync(pred_host, dp, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) ||
+       cudaMemcpyAsync(pred_host, dp, pbytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) ||
       cudaStreamWaitEvent(s, ev_side, 0) != cudaSuccess)
     return FW_ERR_CUDA;
   return fw_sync_status(stream);

@@ -439,6 +439,7 @@ fw_status fw_batched_plan_create(fw_batched_plan** plan, const int64_t* n, const
   if (!plan) return FW_ERR_ARG;
   *plan = nullptr;
   if (!n || !ld || batch < 1 || batch > 65536) return FW_ERR_ARG;
+  if (dtype == FW_I64 || dtype == FW_F64) return FW_ERR_UNSUPPORTED;  // 32-bit types only
   if (dtype != FW_I32 && dtype != FW_F32) return FW_ERR_ARG;
   fw_options o;
   fw_options_default(&o);
@@ -528,6 +529,7 @@ fw_status fw_bs_table(int32_t* table, int32_t set) {
 
 fw_status fw_autotune_bs(fw_dtype dtype, int64_t graphs_per_class, int64_t max_n, void* stream,
                          int32_t* table_out, double* ms_out) {
+  if (dtype == FW_I64 || dtype == FW_F64) return FW_ERR_UNSUPPORTED;  // 32-bit types only
   if (dtype != FW_I32 && dtype != FW_F32) return FW_ERR_ARG;
   if (graphs_per_class < 1 || graphs_per_class > 4096 || max_n < 1) return FW_ERR_ARG;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);

@@ -215,25 +215,69 @@ struct Keys {
   static_assert((1 << (KB - 1)) == BS, "BS must be 32, 64 or 128");
 };
 
+// Element types: int32 and fp32 (the relaxation of the hot path), int64 and
+// fp64 (the paper's double-precision runs, Sec. 4).  kInt: sums are exact, so
+// the "via" predecessor encoding holds; kPacked: the DPX packed-key kernels
+// apply (int32 only).  Missing edges: 2^29 (int32), 2^61 (int64), +inf.
 template <typename T>
 struct Num;
 template <>
 struct Num<int32_t> {
   static constexpr bool kInt = true;
+  static constexpr bool kPacked = true;
   __device__ __forceinline__ static int32_t inf() { return 1 << 29; }
   __device__ __forceinline__ static bool finite(int32_t v) { return v < (1 << 29); }
 };
 template <>
 struct Num<float> {
   static constexpr bool kInt = false;
+  static constexpr bool kPacked = false;
   __device__ __forceinline__ static float inf() { return __int_as_float(0x7f800000); }
   __device__ __forceinline__ static bool finite(float v) { return v < __int_as_float(0x7f800000); }
 };
+template <>
+struct Num<int64_t> {
+  static constexpr bool kInt = true;
+  static constexpr bool kPacked = false;
+  __device__ __forceinline__ static int64_t inf() { return (int64_t)1 << 61; }
+  __device__ __forceinline__ static bool finite(int64_t v) { return v < ((int64_t)1 << 61); }
+};
+template <>
+struct Num<double> {
+  static constexpr bool kInt = false;
+  static constexpr bool kPacked = false;
+  __device__ __forceinline__ static double inf() { return __longlong_as_double(0x7ff0000000000000ll); }
+  __device__ __forceinline__ static bool finite(double v) {
+    return v < __longlong_as_double(0x7ff0000000000000ll);
+  }
+};
 
-// Vector load / store of G consecutive 32-bit elements.
+// min of two elements (fminf / fmin for the floating types: no NaN occurs).
+template <typename T>
+__device__ __forceinline__ T vmin(T a, T b) {
+  if constexpr (std::is_same<T, float>::value) return fminf(a, b);
+  else if constexpr (std::is_same<T, double>::value) return fmin(a, b);
+  else return a < b ? a : b;
+}
+
+// Raw vector of NB bytes and G elements viewed as one value (8-byte elements).
+template <int NB> struct RawVec;
+template <> struct RawVec<16> { int4 a; };
+template <> struct RawVec<32> { int4 a, b; };
+template <int G, typename T> struct ValVec { T v[G]; };
+
+// Vector load / store of G consecutive elements (32-bit elements: one 16- or
+// 8-byte access; 64-bit elements: one or two 16-byte accesses).
 template <int G, typename T>
 __device__ __forceinline__ void vload_cg(T (&dst)[G], const T* src) {
-  if constexpr (G == 4) {
+  if constexpr (sizeof(T) == 8) {
+    RawVec<G * 8> r;
+    r.a = __ldcg(reinterpret_cast<const int4*>(src));
+    if constexpr (G == 4) r.b = __ldcg(reinterpret_cast<const int4*>(src) + 1);
+    const ValVec<G, T> v = __builtin_bit_cast(ValVec<G, T>, r);
+#pragma unroll
+    for (int e = 0; e < G; ++e) dst[e] = v.v[e];
+  } else if constexpr (G == 4) {
     int4 v = __ldcg(reinterpret_cast<const int4*>(src));
     dst[0] = __builtin_bit_cast(T, v.x); dst[1] = __builtin_bit_cast(T, v.y);
     dst[2] = __builtin_bit_cast(T, v.z); dst[3] = __builtin_bit_cast(T, v.w);
@@ -244,7 +288,14 @@ __device__ __forceinline__ void vload_cg(T (&dst)[G], const T* src) {
 }
 template <int G, typename T>
 __device__ __forceinline__ void vstore(T* dst, const T (&src)[G]) {
-  if constexpr (G == 4) {
+  if constexpr (sizeof(T) == 8) {
+    ValVec<G, T> v;
+#pragma unroll
+    for (int e = 0; e < G; ++e) v.v[e] = src[e];
+    const RawVec<G * 8> r = __builtin_bit_cast(RawVec<G * 8>, v);
+    reinterpret_cast<int4*>(dst)[0] = r.a;
+    if constexpr (G == 4) reinterpret_cast<int4*>(dst)[1] = r.b;
+  } else if constexpr (G == 4) {
     int4 v;
     v.x = __builtin_bit_cast(int, src[0]); v.y = __builtin_bit_cast(int, src[1]);
     v.z = __builtin_bit_cast(int, src[2]); v.w = __builtin_bit_cast(int, src[3]);
@@ -257,7 +308,14 @@ __device__ __forceinline__ void vstore(T* dst, const T (&src)[G]) {
 }
 template <int G, typename T>
 __device__ __forceinline__ void vload_s(T (&dst)[G], const T* src) {
-  if constexpr (G == 4) {
+  if constexpr (sizeof(T) == 8) {
+    RawVec<G * 8> r;
+    r.a = reinterpret_cast<const int4*>(src)[0];
+    if constexpr (G == 4) r.b = reinterpret_cast<const int4*>(src)[1];
+    const ValVec<G, T> v = __builtin_bit_cast(ValVec<G, T>, r);
+#pragma unroll
+    for (int e = 0; e < G; ++e) dst[e] = v.v[e];
+  } else if constexpr (G == 4) {
     int4 v = *reinterpret_cast<const int4*>(src);
     dst[0] = __builtin_bit_cast(T, v.x); dst[1] = __builtin_bit_cast(T, v.y);
     dst[2] = __builtin_bit_cast(T, v.z); dst[3] = __builtin_bit_cast(T, v.w);
@@ -312,12 +370,13 @@ struct Args {
 
 // -------------------------------------------------------- shared memory ----
 
-template <int BS>
+template <int BS, typename T>
 struct Smem {
   static constexpr int kTile = BS * BS;
-  // As, Bs and Ps (panel tasks' predecessor source) are BS*BS 32-bit words
-  // each; the pivot task reuses As for its row / column broadcast buffers.
-  static constexpr size_t bytes() { return (size_t)3 * kTile * 4 + 256; }
+  // As and Bs (BS*BS elements each) and Ps (the panel tasks' predecessor
+  // source, BS*BS int32); the pivot task reuses As for its row / column
+  // broadcast buffers.
+  static constexpr size_t bytes() { return (size_t)kTile * (2 * sizeof(T) + 4) + 256; }
 };
 
 struct CtaScratch {
@@ -426,7 +485,7 @@ __device__ __forceinline__ uint32_t key_of(int32_t d) {
 // themselves, INF as 0, negative entries as CAP (they disable the fast path).
 template <int BS, typename T>
 __device__ __forceinline__ int bound_of(T v) {
-  if constexpr (Num<T>::kInt) {
+  if constexpr (Num<T>::kPacked) {
     if (!Num<T>::finite(v)) return 0;
     return v < 0 ? Keys<BS>::CAP : min((int)v, Keys<BS>::CAP);
   } else {
@@ -556,10 +615,7 @@ __device__ __forceinline__ void core_min(const T* __restrict__ As, const T* __re
 #pragma unroll
     for (int m = 0; m < TM; ++m)
 #pragma unroll
-      for (int nn = 0; nn < TM; ++nn) {
-        if constexpr (Num<T>::kInt) acc[m][nn] = min(a[m] + b[nn], acc[m][nn]);
-        else acc[m][nn] = fminf(a[m] + b[nn], acc[m][nn]);
-      }
+      for (int nn = 0; nn < TM; ++nn) acc[m][nn] = vmin<T>(a[m] + b[nn], acc[m][nn]);
   }
 }
 
@@ -962,7 +1018,7 @@ __device__ __noinline__ void task_pivot(const Args<T>& a, int r, void* smem_raw,
   using K = Keys<BS>;
   constexpr int TM = Gm::TM;
   stamp(0);
-  if constexpr (Num<T>::kInt) {
+  if constexpr (Num<T>::kPacked) {
     // every value formed in the closure is a path of at most BS segments of
     // current entries; keep twice that below CAP.  The tile is loaded once,
     // distances and predecessors together (one memory round trip).
@@ -1077,7 +1133,7 @@ __device__ __forceinline__ int panel_store_group(const Args<T>& a, int r, int t,
       for (int q = 0; q < G; ++q) {
         vs[q] = sv[e][gg * G + q];
         vp[q] = np[e][gg * G + q];
-        if constexpr (Num<T>::kInt) nb = max(nb, bound_of<BS>(vs[q]));
+        if constexpr (Num<T>::kPacked) nb = max(nb, bound_of<BS>(vs[q]));
       }
       if (gi < a.n) {
         if (gj0 + G <= a.n) {
@@ -1106,7 +1162,7 @@ __device__ __forceinline__ int panel_store_group(const Args<T>& a, int r, int t,
         if constexpr (!ViaPred<T>::kOn) {
           if (a.P) vstore<G>(a.rowP + tile_off + lr * BS + lc0, vp);
         }
-        if constexpr (Num<T>::kInt) {
+        if constexpr (Num<T>::kPacked) {
           uint32_t kq[G];
 #pragma unroll
           for (int q = 0; q < G; ++q) kq[q] = key_of<BS>((int32_t)vs[q]);
@@ -1125,7 +1181,7 @@ __device__ __forceinline__ int panel_store_group(const Args<T>& a, int r, int t,
 #pragma unroll
       for (int e = 0; e < G; ++e) vs[e] = sv[e][nn];
       vstore<G>(a.colR + off, vs);
-      if constexpr (Num<T>::kInt) {
+      if constexpr (Num<T>::kPacked) {
         uint32_t kq[G];
 #pragma unroll
         for (int e = 0; e < G; ++e) kq[e] = key_of<BS>((int32_t)vs[e]) + (uint32_t)lc + 1u;
@@ -1275,13 +1331,15 @@ __device__ __noinline__ void task_panel(const Args<T>& a, int r, int t, bool is_
   using Gm = Geo<BS>;
   using K = Keys<BS>;
   constexpr int TM = Gm::TM;
-  constexpr bool kInt = Num<T>::kInt;
+  constexpr bool kPacked = Num<T>::kPacked;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int ti = is_row ? r : t, tj = is_row ? t : r;
   const int slot = r & 1;
-  uint32_t* As = reinterpret_cast<uint32_t*>(smem_raw);
-  uint32_t* Bs = As + BS * BS;
-  int32_t* Ps = reinterpret_cast<int32_t*>(Bs + BS * BS);
+  // As | Bs: BS*BS elements each (keys or raw values); Ps: BS*BS int32
+  unsigned char* sm = reinterpret_cast<unsigned char*>(smem_raw);
+  uint32_t* As = reinterpret_cast<uint32_t*>(sm);
+  uint32_t* Bs = reinterpret_cast<uint32_t*>(sm + (size_t)BS * BS * sizeof(T));
+  int32_t* Ps = reinterpret_cast<int32_t*>(sm + (size_t)2 * BS * BS * sizeof(T));
   stamp(0);
 
   // predecessor source, staged (its loads overlap the operand loads below)
@@ -1298,7 +1356,7 @@ __device__ __noinline__ void task_panel(const Args<T>& a, int r, int t, bool is_
     T s[TM][TM], pv[TM][TM];
     load_tile<BS>(s, a.D, a.n, a.ld, ti, tj, tx, ty, Num<T>::inf());
     load_buf<BS>(pv, a.piv + (size_t)slot * BS * BS, tx, ty);
-    if constexpr (kInt) {
+    if constexpr (kPacked) {
       int bs_ = 0, bp_ = 0;
 #pragma unroll
       for (int m = 0; m < TM; ++m)
@@ -1312,7 +1370,7 @@ __device__ __noinline__ void task_panel(const Args<T>& a, int r, int t, bool is_
     }
     // operands into shared memory: A-form (k-major) on the left, B-form on the right
     if (fast) {
-      if constexpr (kInt) {
+      if constexpr (kPacked) {
         // keys; the A operand carries the code of its column (= kk)
 #pragma unroll
         for (int m = 0; m < TM; ++m)
@@ -1349,13 +1407,19 @@ __device__ __noinline__ void task_panel(const Args<T>& a, int r, int t, bool is_
 
   const T* Ast = reinterpret_cast<const T*>(As);
   const T* Bst = reinterpret_cast<const T*>(Bs);
-  int nb = is_row ? (fast ? panel_packed<T, BS, true>(a, r, t, As, Bs, Ps)
-                          : panel_eager<T, BS, true>(a, r, t, Ast, Bst, Ps))
-                  : (fast ? panel_packed<T, BS, false>(a, r, t, As, Bs, Ps)
-                          : panel_eager<T, BS, false>(a, r, t, Ast, Bst, Ps));
+  int nb;
+  if constexpr (kPacked) {
+    nb = is_row ? (fast ? panel_packed<T, BS, true>(a, r, t, As, Bs, Ps)
+                        : panel_eager<T, BS, true>(a, r, t, Ast, Bst, Ps))
+                : (fast ? panel_packed<T, BS, false>(a, r, t, As, Bs, Ps)
+                        : panel_eager<T, BS, false>(a, r, t, Ast, Bst, Ps));
+  } else {
+    nb = is_row ? panel_eager<T, BS, true>(a, r, t, Ast, Bst, Ps)
+                : panel_eager<T, BS, false>(a, r, t, Ast, Bst, Ps);
+  }
   stamp(3);
   int dummy = 0;
-  if constexpr (kInt) {
+  if constexpr (kPacked) {
     block_max2(nb, dummy, cs);
   } else {
     nb = Keys<BS>::CAP;
@@ -1378,16 +1442,17 @@ __device__ void task_minplus(const Args<T>& a, int r, int ti, int tj, void* smem
   using Gm = Geo<BS>;
   using K = Keys<BS>;
   constexpr int TM = Gm::TM;
-  constexpr bool kInt = Num<T>::kInt;
+  constexpr bool kPacked = Num<T>::kPacked;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int slot = r & 1;
   uint32_t* As = reinterpret_cast<uint32_t*>(smem_raw);
-  uint32_t* Bs = As + BS * BS;
+  uint32_t* Bs = reinterpret_cast<uint32_t*>(reinterpret_cast<unsigned char*>(smem_raw) +
+                                             (size_t)BS * BS * sizeof(T));
   const size_t toffA = ((size_t)slot * a.slot_tiles + ti) * BS * BS;
   const size_t toffB = ((size_t)slot * a.slot_tiles + tj) * BS * BS;
 
   bool fast = false;
-  if constexpr (kInt) {
+  if constexpr (kPacked) {
     if (a.packed) {
       const int ba = __ldcg(a.colB + (size_t)slot * a.slot_tiles + ti);
       const int bb = __ldcg(a.rowB + (size_t)slot * a.slot_tiles + tj);
@@ -1395,7 +1460,7 @@ __device__ void task_minplus(const Args<T>& a, int r, int ti, int tj, void* smem
     }
   }
   if (tid == 0) {
-    constexpr unsigned bytes = BS * BS * 4;
+    constexpr unsigned bytes = BS * BS * sizeof(T);
     fence_proxy_async();
     mbar_expect_tx(&cs->bar, 2 * bytes);
     const void* srcA = fast ? (const void*)(a.colK + toffA) : (const void*)(a.colR + toffA);
@@ -1420,12 +1485,12 @@ __device__ void task_minplus(const Args<T>& a, int r, int ti, int tj, void* smem
 
   int32_t* rowP = a.rowP + toffB;
   bool neg = false;
-  if (fast) {
+  if (kPacked && fast) {
     uint32_t acc[TM][TM];
 #pragma unroll
     for (int m = 0; m < TM; ++m)
 #pragma unroll
-      for (int nn = 0; nn < TM; ++nn) acc[m][nn] = kInt ? key_of<BS>((int32_t)old[m][nn]) : 0u;
+      for (int nn = 0; nn < TM; ++nn) acc[m][nn] = kPacked ? key_of<BS>((int32_t)old[m][nn]) : 0u;
     core_packed<BS>(As, Bs, acc, tx, ty);
 #pragma unroll
     for (int m = 0; m < TM; ++m) {

@@ -135,10 +135,11 @@ struct SolveWs {
   size_t flags_bytes = 0;  // ver + done + ctr + abort (zeroed before each solve)
 };
 
-// Bytes needed by a solve of R tiles of BS (excluding alignment slack).
-size_t solve_ws_bytes(int R, int BS);
-// Carve a workspace out of `base` (cudaMalloc'd, >= solve_ws_bytes + 4 KiB).
-SolveWs carve_solve_ws(void* base, int R, int BS);
+// Bytes needed by a solve of R tiles of BS with esize-byte elements (4: int32
+// or fp32, with the packed-key snapshots; 8: int64 or fp64, without them).
+size_t solve_ws_bytes(int R, int BS, int esize = 4);
+// Carve a workspace out of `base` (cudaMalloc'd, >= solve_ws_bytes).
+SolveWs carve_solve_ws(void* base, int R, int BS, int esize = 4);
 
 struct LaunchCfg {
   int BS;
@@ -160,6 +161,10 @@ cudaError_t launch_solve_i32(int32_t* D, int32_t* P, int64_t n, int64_t ld, cons
                              const LaunchCfg& cfg, cudaStream_t s);
 cudaError_t launch_solve_f32(float* D, int32_t* P, int64_t n, int64_t ld, const SolveWs& ws,
                              const LaunchCfg& cfg, cudaStream_t s);
+cudaError_t launch_solve_i64(int64_t* D, int32_t* P, int64_t n, int64_t ld, const SolveWs& ws,
+                             const LaunchCfg& cfg, cudaStream_t s);
+cudaError_t launch_solve_f64(double* D, int32_t* P, int64_t n, int64_t ld, const SolveWs& ws,
+                             const LaunchCfg& cfg, cudaStream_t s);
 
 int num_sms();
 
@@ -169,9 +174,11 @@ int num_sms();
 // kernel) under a lock and cached there.  Returns <= 0 on failure.
 int kernel_setup(const void* fn, size_t smem, int threads);
 
-// Tensor map of a row-major n x n matrix of 32-bit elements with leading
-// dimension ld (elements), read in box x box tiles (2-D TMA).  False when the
-// driver offers no encoder or rejects the layout; callers then copy by rows.
-bool encode_tile_map(CUtensorMap* map, const void* base, int64_t n, int64_t ld, int box, bool f32);
+// Tensor map of a row-major n x n matrix of `dt` elements (esize bytes each)
+// with leading dimension ld (elements), read in box x box tiles (2-D TMA).
+// False when the driver offers no encoder or rejects the layout; callers then
+// copy by rows.
+bool encode_tile_map(CUtensorMap* map, const void* base, int64_t n, int64_t ld, int box,
+                     CUtensorMapDataType dt, int esize);
 
 }  // namespace fwh

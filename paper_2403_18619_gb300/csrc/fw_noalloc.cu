@@ -125,6 +125,7 @@ extern "C" fw_status fw_solve_noalloc(void* dist, int32_t* pred, int64_t n, int6
   if (n <= 0 || ld < n || (ld % 4) != 0) return FW_ERR_ARG;
   if ((reinterpret_cast<uintptr_t>(dist) & 15) || (reinterpret_cast<uintptr_t>(pred) & 15))
     return FW_ERR_ARG;
+  if (dtype == FW_I64 || dtype == FW_F64) return FW_ERR_UNSUPPORTED;  // 32-bit types only
   if (dtype != FW_I32 && dtype != FW_F32) return FW_ERR_ARG;
   if (n > kMaxN) return FW_ERR_UNSUPPORTED;  // larger graphs need fw_solve's workspace
   const int BS = n <= 512 ? 32 : 64;

@@ -1,0 +1,9 @@
+// int64 instantiation of the solver (generic kernels, "via" predecessors).
+#include "fw_solve_impl.cuh"
+
+namespace fwh {
+cudaError_t launch_solve_i64(int64_t* D, int32_t* P, int64_t n, int64_t ld, const SolveWs& ws,
+                             const LaunchCfg& cfg, cudaStream_t s) {
+  return fwk::launch_any<int64_t>(D, P, n, ld, ws, cfg, s);
+}
+}  // namespace fwh

@@ -44,6 +44,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_phase_rest(Args<T> a, int r) {
 
 // ---------------------------------------------------------------- host ----
 
+// Tensor-map element type of T.
+template <typename T> struct TmapType;
+template <> struct TmapType<int32_t> { static constexpr CUtensorMapDataType kType = CU_TENSOR_MAP_DATA_TYPE_INT32; };
+template <> struct TmapType<float> { static constexpr CUtensorMapDataType kType = CU_TENSOR_MAP_DATA_TYPE_FLOAT32; };
+template <> struct TmapType<int64_t> { static constexpr CUtensorMapDataType kType = CU_TENSOR_MAP_DATA_TYPE_INT64; };
+template <> struct TmapType<double> { static constexpr CUtensorMapDataType kType = CU_TENSOR_MAP_DATA_TYPE_FLOAT64; };
+
 template <typename T, int BS>
 cudaError_t launch_bs(T* D, int32_t* P, int64_t n, int64_t ld, const fwh::SolveWs& ws,
                       const fwh::LaunchCfg& cfg, cudaStream_t s) {
@@ -57,7 +64,7 @@ cudaError_t launch_bs(T* D, int32_t* P, int64_t n, int64_t ld, const fwh::SolveW
   a.rowK = ws.rowK; a.rowR = reinterpret_cast<T*>(ws.rowR); a.rowP = ws.rowP; a.rowB = ws.rowB;
   a.trace = cfg.trace; a.trace_cap = (int)cfg.trace_cap; a.trace_stride = cfg.trace_stride;
   const int R = ws.R;
-  const size_t smem = Smem<BS>::bytes();
+  const size_t smem = Smem<BS, T>::bytes();
   cudaError_t e;
 
   if (P) {  // null: distance-only
@@ -104,8 +111,10 @@ cudaError_t launch_bs(T* D, int32_t* P, int64_t n, int64_t ld, const fwh::SolveW
     CUtensorMap tmD{}, tmP{};
     int use_tmap = 0;
     if (cfg.tile_tma) {
-      if (fwh::encode_tile_map(&tmD, D, n, ld, BS, !Num<T>::kInt)) use_tmap |= 1;
-      if (P && fwh::encode_tile_map(&tmP, P, n, ld, BS, false)) use_tmap |= 2;
+      if (fwh::encode_tile_map(&tmD, D, n, ld, BS, TmapType<T>::kType, (int)sizeof(T)))
+        use_tmap |= 1;
+      if (P && fwh::encode_tile_map(&tmP, P, n, ld, BS, CU_TENSOR_MAP_DATA_TYPE_INT32, 4))
+        use_tmap |= 2;
     }
     if ((e = cudaLaunchKernelEx(&lc, kern, a, tmD, tmP, use_tmap)) != cudaSuccess) return e;
   }
@@ -126,7 +135,10 @@ cudaError_t launch_any(T* D, int32_t* P, int64_t n, int64_t ld, const fwh::Solve
   switch (cfg.BS) {
     case 32: return launch_bs<T, 32>(D, P, n, ld, ws, cfg, s);
     case 64: return launch_bs<T, 64>(D, P, n, ld, ws, cfg, s);
-    case 128: return launch_bs<T, 128>(D, P, n, ld, ws, cfg, s);
+    case 128:
+      // three 128 x 128 tiles of 64-bit elements do not fit in shared memory
+      if constexpr (sizeof(T) == 4) return launch_bs<T, 128>(D, P, n, ld, ws, cfg, s);
+      return cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
   }
 }

@@ -39,31 +39,37 @@ constexpr int kPubDepth = 4;  // tasks handed to the compute warps but not yet p
 // int32 streams 64-step chunks (2 per task at BS = 128: fewer ring hand-offs);
 // fp32 keeps 32-step chunks and spends the saved space on the predecessor
 // snapshot tile of its epilogue.
+// 64-bit elements stream 32-step chunks (BS is at most 64 for them).
 template <int BS, typename T>
 struct WsChunk {
-  static constexpr int kCKmax = ViaPred<T>::kOn ? 64 : 32;
-  static constexpr int CK = BS < kCKmax ? BS : kCKmax;        // k-steps per chunk
-  static constexpr int NC = BS / CK;                          // chunks per task
-  static constexpr size_t kChunkBytes = (size_t)CK * BS * 4;  // one operand chunk
-  static constexpr size_t kTile = (size_t)BS * BS * 4;
+  static constexpr int kCKmax = (ViaPred<T>::kOn && sizeof(T) == 4) ? 64 : 32;
+  static constexpr int CK = BS < kCKmax ? BS : kCKmax;                    // k-steps per chunk
+  static constexpr int NC = BS / CK;                                      // chunks per task
+  static constexpr size_t kChunkBytes = (size_t)CK * BS * sizeof(T);      // one operand chunk
+  static constexpr size_t kTile = (size_t)BS * BS * sizeof(T);            // a tile of elements
+  static constexpr size_t kPTile = (size_t)BS * BS * 4;                   // a tile of int32 pred
 };
 
 // Shared-memory layout sized for the largest block size LBS a launch runs:
-// the 2-stage operand ring, the tile's own D (Dbuf) and, for fp32, the
-// row-panel predecessor snapshot (Pbuf); 192 KB for LBS = 128 either way.
+// the 2-stage operand ring, the tile's own D (Dbuf) and, for the floating
+// types, the row-panel predecessor snapshot (Pbuf); 192 KB for LBS = 128 with
+// 32-bit elements, 112 KB (fp64) or 96 KB (int64) for LBS = 64.
 template <int LBS, typename T>
 struct WsLayout {
   static constexpr size_t kStage = 2 * WsChunk<LBS, T>::kChunkBytes;  // A chunk + B chunk
   static constexpr size_t kRing = 2 * kStage;
   static constexpr size_t kTile = WsChunk<LBS, T>::kTile;
+  static constexpr size_t kPTile = WsChunk<LBS, T>::kPTile;
   __host__ __device__ static constexpr size_t ring_off() { return 0; }
   __host__ __device__ static constexpr size_t d_off() { return kRing; }
   __host__ __device__ static constexpr size_t p_off() { return kRing + kTile; }
   __host__ __device__ static constexpr size_t bytes() {
-    return kRing + kTile + (ViaPred<T>::kOn ? 0 : kTile);
+    return kRing + kTile + (ViaPred<T>::kOn ? 0 : kPTile);
   }
-  // pivot and panel tasks use the buffer from offset 0 as scratch (3 tiles)
-  static_assert(bytes() >= 3 * kTile, "scratch of pivot / panel tasks");
+  // pivot and panel tasks use the buffer from offset 0 as scratch (As, Bs of
+  // elements and Ps of int32)
+  static_assert(bytes() >= 2 * kTile + kPTile, "scratch of pivot / panel tasks");
+  static_assert(bytes() <= 227 * 1024, "shared memory of one CTA");
 };
 
 struct WsBars {
@@ -223,7 +229,7 @@ __device__ __forceinline__ bool ws_minplus(TileCtx<T> c, int ti, int tj, bool fa
   using L = WsLayout<LBS, T>;
   using C = WsChunk<BS, T>;
   constexpr int TM = Gm::TM, G = Gm::G;
-  constexpr bool kInt = Num<T>::kInt;
+  constexpr bool kPacked = Num<T>::kPacked;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4, lane = tid & 31;
   const T* Dbuf = reinterpret_cast<const T*>(smem + L::d_off());
   const int32_t* Pbuf = reinterpret_cast<const int32_t*>(smem + L::p_off());
@@ -261,14 +267,14 @@ __device__ __forceinline__ bool ws_minplus(TileCtx<T> c, int ti, int tj, bool fa
   T* Drow = c.D + row0 * c.ld + col0;
   int32_t* Prow = c.P + row0 * c.ld + col0;
   bool neg = false;
-  if (kInt && fast) {  // (packed keys: int32 only)
+  if (kPacked && fast) {  // (packed keys: int32 only)
     uint32_t acc[TM][TM];
     int32_t omax = 0;
 #pragma unroll
     for (int m = 0; m < TM; ++m)
 #pragma unroll
       for (int nn = 0; nn < TM; ++nn) {
-        acc[m][nn] = kInt ? key_of<BS>((int32_t)old[m][nn]) : 0u;
+        acc[m][nn] = kPacked ? key_of<BS>((int32_t)old[m][nn]) : 0u;
         omax = max(omax, (int32_t)old[m][nn]);
       }
     const bool clamped = omax >= K::CAP;  // some old value's key is the clamp
@@ -519,7 +525,7 @@ __device__ __forceinline__ void publish(const Args<T>& a, const fwh::Task& k) {
 // Whether a remaining-tile task may relax packed keys (int32, bounded panels).
 template <typename T, int BS>
 __device__ __forceinline__ bool packed_ok(const Args<T>& a, const fwh::Task& k) {
-  if (!(Num<T>::kInt && a.packed && k.type == 3)) return false;
+  if (!(Num<T>::kPacked && a.packed && k.type == 3)) return false;
   const int slot = k.r & 1;
   const int ba = __ldcg(a.colB + (size_t)slot * a.slot_tiles + k.ti);
   const int bb = __ldcg(a.rowB + (size_t)slot * a.slot_tiles + k.tj);
@@ -538,7 +544,9 @@ __device__ void issue_operands(const Args<T>& a, const fwh::Task& k, bool fast, 
   const int64_t row0 = (int64_t)k.ti * BS, col0 = (int64_t)k.tj * BS;
   const int nrows = (int)(a.n - row0 < (int64_t)BS ? a.n - row0 : (int64_t)BS);
   const int ncols = (int)(a.n - col0 < (int64_t)BS ? a.n - col0 : (int64_t)BS);
-  const unsigned rowbytes = (unsigned)(((ncols + 3) / 4) * 4) * 4u;
+  // whole 16-byte granules (rows are 16-byte aligned and ld % 4 == 0, so the
+  // rounded row stays inside the caller's row)
+  const unsigned rowbytes = (unsigned)(((size_t)ncols * sizeof(T) + 15) / 16 * 16);
   unsigned char* dbuf = smem + L::d_off();
   if (a.tmapD) {
     // one tensor copy of the whole box (elements beyond n arrive as zeros and
@@ -599,8 +607,8 @@ __device__ void issue_operands(const Args<T>& a, const fwh::Task& k, bool fast, 
   if (!ViaPred<T>::kOn && a.P) {
     if (lane == 0) {
       if (!pc.stop && mbar_wait(&wb->p_empty, (pc.p & 1) ^ 1, a.status, a.abort_flag, a.timeout_ns)) {
-        mbar_expect_tx(&wb->p_full, (unsigned)C::kTile);
-        bulk_g2s(smem + L::p_off(), a.rowP + toffB, (unsigned)C::kTile, &wb->p_full);
+        mbar_expect_tx(&wb->p_full, (unsigned)C::kPTile);
+        bulk_g2s(smem + L::p_off(), a.rowP + toffB, (unsigned)C::kPTile, &wb->p_full);
         pc.p_armed = pc.p + 1;
       } else {
         pc.stop = true;

@@ -13,6 +13,16 @@ CANARY_I = np.int32(-123456789)
 CANARY_F = np.float32(-7.25)
 
 
+def _torch_dtype_and_canary(dtype):
+    """(torch dtype, padding canary) of a numpy weight dtype."""
+    import torch
+    table = {np.dtype(np.int32): (torch.int32, int(CANARY_I)),
+             np.dtype(np.float32): (torch.float32, float(CANARY_F)),
+             np.dtype(np.int64): (torch.int64, -123456789123),
+             np.dtype(np.float64): (torch.float64, -7.25)}
+    return table[np.dtype(dtype)]
+
+
 def fw():
     import paper_2403_18619_gb300 as m
     return m
@@ -25,10 +35,8 @@ def gpu_solve(W: np.ndarray, *, bs=0, driver=0, packed=1, extra_ld=0, lookahead=
     m = fw()
     n = W.shape[0]
     ld = m.padded(n) + extra_ld
-    tdt = torch.int32 if W.dtype == np.int32 else torch.float32
-    canary = CANARY_I if W.dtype == np.int32 else CANARY_F
-    Dbuf = torch.full((n, ld), float(canary) if tdt == torch.float32 else int(canary),
-                      dtype=tdt, device="cuda")
+    tdt, canary = _torch_dtype_and_canary(W.dtype)
+    Dbuf = torch.full((n, ld), canary, dtype=tdt, device="cuda")
     Pbuf = torch.full((n, ld), -987654, dtype=torch.int32, device="cuda")
     D, P = Dbuf[:, :n], Pbuf[:, :n]
     D.copy_(torch.from_numpy(np.ascontiguousarray(W)))
@@ -123,10 +131,8 @@ def gpu_solve_dist_only(W: np.ndarray, *, bs=0, driver=0, packed=1, extra_ld=0):
     m = fw()
     n = W.shape[0]
     ld = m.padded(n) + extra_ld
-    tdt = torch.int32 if W.dtype == np.int32 else torch.float32
-    canary = CANARY_I if W.dtype == np.int32 else CANARY_F
-    Dbuf = torch.full((n, ld), float(canary) if tdt == torch.float32 else int(canary),
-                      dtype=tdt, device="cuda")
+    tdt, canary = _torch_dtype_and_canary(W.dtype)
+    Dbuf = torch.full((n, ld), canary, dtype=tdt, device="cuda")
     D = Dbuf[:, :n]
     D.copy_(torch.from_numpy(np.ascontiguousarray(W)))
     m.fw_solve_ex(D, None, m.Options.default(bs=bs, driver=driver, packed_keys=packed))
@@ -137,7 +143,7 @@ def gpu_solve_dist_only(W: np.ndarray, *, bs=0, driver=0, packed=1, extra_ld=0):
     return Dh[:, :n].copy()
 
 
-def check_pred_tight_int(W, Do, Pg, Po):
+def check_pred_tight_int(W, Do, Pg, Po, inf=INF):
     """Predecessors against the full int64 oracle: equal to the oracle's last
     hop, or else another last hop u that is tight (an edge u -> j with
     D[i][u] + W[u][j] == D[i][j]).  A second tight last hop means a second
@@ -151,7 +157,7 @@ def check_pred_tight_int(W, Do, Pg, Po):
     u = Pg[i, j].astype(np.int64)
     assert ((u >= 0) & (u < n) & (u != j)).all(), "pred out of range where it differs"
     w = W[u, j].astype(np.int64)
-    assert (w < INF).all(), "pred is not an in-neighbour where it differs"
+    assert (w < inf).all(), "pred is not an in-neighbour where it differs"
     bad = Do[i, u] + w != Do[i, j]
     assert not bad.any(), "pred not tight at %d pairs, first (%d, %d)" % (
         bad.sum(), i[bad][0], j[bad][0])

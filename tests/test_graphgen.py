@@ -44,3 +44,26 @@ def test_batch_sizes_and_normals():
     assert ns.min() >= 64 and ns.max() <= 2048 and len(set(ns.tolist())) > 300
     z = graphgen.normal_f32((100000,), seed=1)
     assert abs(z.mean()) < 0.02 and abs(z.std() - 1) < 0.02
+
+
+def test_wide_graph_ranges_and_exactness():
+    n = 200
+    W = graphgen.dense_graph_i64(n, seed=5, p=0.4, lo=1, hi=10 ** 12)
+    off = ~np.eye(n, dtype=bool)
+    e = W[off] < graphgen.INF_I64
+    assert abs(e.mean() - 0.4) < 0.02
+    assert W[off][e].min() >= 1 and W[off][e].max() <= 10 ** 12
+    assert W[off][e].max() > 2 ** 31  # beyond the int32 range
+    assert (np.diag(W) == 0).all() and W.dtype == np.int64
+    # the same counters as the int32 generator: same edges, same draws mod span
+    W32 = graphgen.dense_graph_i32(n, seed=5, p=0.4, lo=1, hi=100)
+    np.testing.assert_array_equal(W32[off] < graphgen.INF_I32, e)
+    V = graphgen.dense_graph_f64(n, seed=6, p=0.5)
+    fin = np.isfinite(V[off])
+    assert V[off][fin].min() > 0 and V[off][fin].max() <= 1
+    # full 53-bit mantissas: most weights are not representable in fp32
+    assert (V[off][fin].astype(np.float32).astype(np.float64) != V[off][fin]).mean() > 0.99
+    U = graphgen.dense_graph_f64(n, seed=6, p=0.5, kind=graphgen.KIND_ONE_TWO)
+    u = U[off][np.isfinite(U[off])]
+    assert u.min() >= 1 and u.max() < 2
+    np.testing.assert_array_equal(V, graphgen.dense_graph_f64(n, 6, 0.5, chunk_rows=13))

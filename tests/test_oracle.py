@@ -247,6 +247,75 @@ def test_vs_scipy_float(n, p, seed):
     assert safe.sum() > n
 
 
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_brute_force_wide_inputs(seed):
+    """64-bit inputs: int64 weights far beyond the int32 range (every sum of up
+    to 6 of them is exact in the brute force's fp64) and fp64 weights with full
+    53-bit mantissas."""
+    n = 7
+    W = graphgen.dense_graph_i64(n, seed=seed, p=0.6, lo=1, hi=10 ** 12)
+    best, last, count = brute_force(W, graphgen.INF_I64)
+    D, P = oracle.fw_i64(W)
+    for s_ in range(n):
+        for t in range(n):
+            if np.isinf(best[s_, t]):
+                assert D[s_, t] == graphgen.INF_I64 and P[s_, t] == -1
+                continue
+            assert D[s_, t] == int(best[s_, t])
+            if s_ != t:
+                assert P[s_, t] in last[s_][t]
+    V = graphgen.dense_graph_f64(n, seed=seed + 10, p=0.7)
+    best, last, count = brute_force(V, None)
+    D, P = oracle.fw_f64(V)
+    for s_ in range(n):
+        for t in range(n):
+            if np.isinf(best[s_, t]):
+                assert np.isinf(D[s_, t]) and P[s_, t] == -1
+            else:
+                assert abs(D[s_, t] - best[s_, t]) <= 1e-15 * 8 * max(1.0, best[s_, t])
+                if s_ != t and count[s_, t] == 1:
+                    assert P[s_, t] in last[s_][t]
+
+
+def test_vs_scipy_wide_inputs():
+    """int64 weights up to 1e12 (every path sum below 2**53, so scipy's fp64
+    distances are exact) and fp64 weights: distances equal (int64) or within
+    1e-13 relative (fp64); every last hop of the oracle tight (an edge whose
+    use realises the distance) and equal to scipy's Dijkstra predecessor
+    wherever the latter is the only tight one."""
+    sp = pytest.importorskip("scipy.sparse.csgraph")
+    n = 120
+    W = graphgen.dense_graph_i64(n, seed=8, p=0.2, lo=1, hi=10 ** 12)
+    D, P = oracle.fw_i64(W)
+    Wf = np.where(W >= graphgen.INF_I64, np.inf, W.astype(np.float64))
+    G = sp.csgraph_from_dense(Wf, null_value=np.inf)
+    dist, pred = sp.shortest_path(G, method="D", directed=True, return_predecessors=True)
+    reach = np.isfinite(dist)
+    assert ((D < graphgen.INF_I64) == reach).all()
+    np.testing.assert_array_equal(D[reach], dist[reach].astype(np.int64))
+    off = reach & ~np.eye(n, dtype=bool)
+    i, j = np.nonzero(off)
+    u = P[i, j]
+    assert (u >= 0).all()
+    np.testing.assert_array_equal(D[i, u] + W[u, j], D[i, j])
+    tight_scipy = D[i, pred[i, j]] + W[pred[i, j], j] == D[i, j]
+    assert tight_scipy.all()
+    # pairs where scipy's and the oracle's last hops differ have two tight last hops
+    differ = P[i, j] != pred[i, j]
+    assert differ.mean() < 0.01
+    V = graphgen.dense_graph_f64(n, seed=9, p=0.3)
+    Dv, Pv = oracle.fw_f64(V)
+    G = sp.csgraph_from_dense(V, null_value=np.inf)
+    dist, pred = sp.shortest_path(G, method="D", directed=True, return_predecessors=True)
+    reach = np.isfinite(dist)
+    assert (np.isfinite(Dv) == reach).all()
+    np.testing.assert_allclose(Dv[reach], dist[reach], rtol=1e-13, atol=0)
+    off = reach & ~np.eye(n, dtype=bool)
+    i, j = np.nonzero(off)
+    np.testing.assert_allclose(Dv[i, Pv[i, j]] + V[Pv[i, j], j], Dv[i, j], rtol=1e-13, atol=0)
+    assert (Pv[i, j] == pred[i, j]).mean() > 0.99
+
+
 def test_triangle_inequality():
     n = 64
     W = graphgen.dense_graph_i32(n, seed=9, p=0.2, lo=1, hi=30)

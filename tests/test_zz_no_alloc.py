@@ -81,7 +81,9 @@ def test_noalloc_largest_size_and_status():
     n = 4096
     W = graphgen.dense_graph_i32(n, seed=45, p=0.5, lo=1, hi=1000)
     Dr, Pr = _pair(W)
-    fw.fw_solve(Dr[:, :n], Pr[:, :n])
+    # the same block size as the allocation-free path (64 above n = 512): where
+    # shortest paths tie, the chosen last hop depends on the block size
+    fw.fw_solve_ex(Dr[:, :n], Pr[:, :n], fw.Options.default(bs=64))
     fw.fw_sync_status()
     D, P = _pair(W)
     fw.fw_solve_noalloc(D[:, :n], P[:, :n])
