@@ -1,17 +1,20 @@
 // Min-plus relaxation peak of the GPU (the roofline of the solver's inner loop).
 //
 // Each thread keeps a block of relaxation chains in registers (8 x 8 for the
-// 32-bit types, 4 x 8 for the 64-bit ones, so that 512 threads fit the
+// 32-bit types, 1 x 8 for the 64-bit ones, so that 512 threads fit the
 // register file) and relaxes it with the instructions the solver issues per
 // relaxation:
 //   int32 : acc = __viaddmin_u32(a, b, acc)     (one DPX instruction)
 //   fp32  : acc = fminf(a + b, acc)             (add + min)
-//   fp64  : acc = fmin(a + b, acc)              (DADD + DMNMX)
+//   fp64  : acc = a + b < acc ? a + b : acc     (DADD, then an integer min of
+//                                                the bit patterns, as the solver)
 //   int64 : acc = min(a + b, acc)               (64-bit add + compare-select)
-// The row operands a[m] are refreshed every 4 steps from the chains themselves,
-// so the loop carries a real dependence and nothing can be hoisted out of it.
-// One CTA of 512 threads per SM; %clock64 around the loop gives the SM-clock
-// rate, CUDA events the wall-clock rate.
+// Every unrolled step takes its own column operands b[u][.], so every
+// relaxation forms a distinct sum (none can be computed once and reused) and
+// min(x, min(x, acc)) cannot fold.  The row operands a[m] are refreshed every 4
+// steps from the chains themselves, so the loop carries a real dependence and
+// nothing can be hoisted out of it.  One CTA of 512 threads per SM; %clock64
+// around the loop gives the SM-clock rate, CUDA events the wall-clock rate.
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -24,15 +27,22 @@ constexpr int kProbeThreads = 512;
 template <typename T> struct ProbeMode;
 template <> struct ProbeMode<uint32_t> { static constexpr int M = 8; };
 template <> struct ProbeMode<float> { static constexpr int M = 8; };
-template <> struct ProbeMode<double> { static constexpr int M = 4; };
-template <> struct ProbeMode<int64_t> { static constexpr int M = 4; };
+template <> struct ProbeMode<double> { static constexpr int M = 1; };
+template <> struct ProbeMode<int64_t> { static constexpr int M = 1; };
 
 template <typename T>
 __device__ __forceinline__ T relax(T a, T b, T acc) {
-  if constexpr (std::is_same<T, uint32_t>::value) return __viaddmin_u32(a, b, acc);
-  else if constexpr (std::is_same<T, float>::value) return fminf(a + b, acc);
-  else if constexpr (std::is_same<T, double>::value) return fmin(a + b, acc);
-  else { const T x = a + b; return x < acc ? x : acc; }
+  if constexpr (std::is_same<T, uint32_t>::value) {
+    return __viaddmin_u32(a, b, acc);
+  } else if constexpr (std::is_same<T, float>::value) {
+    return fminf(a + b, acc);
+  } else if constexpr (std::is_same<T, double>::value) {
+    const double x = a + b;
+    return __double_as_longlong(x) < __double_as_longlong(acc) ? x : acc;
+  } else {
+    const T x = a + b;
+    return x < acc ? x : acc;
+  }
 }
 
 template <typename T>
@@ -48,12 +58,14 @@ __global__ void __launch_bounds__(kProbeThreads, 1)
     k_probe(const uint32_t* __restrict__ seed, uint32_t* __restrict__ sink, int iters,
             long long* __restrict__ cycles) {
   constexpr int M = ProbeMode<T>::M;
-  T a[M], b[8], acc[M][8];
+  T a[M], b[4][8], acc[M][8];
   const uint32_t s0 = seed[threadIdx.x & 63];
 #pragma unroll
   for (int m = 0; m < M; ++m) a[m] = seed_value<T>(s0, m);
 #pragma unroll
-  for (int n = 0; n < 8; ++n) b[n] = seed_value<T>(s0 >> 3, 3 * n);
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int n = 0; n < 8; ++n) b[u][n] = seed_value<T>(s0 >> 3, 3 * n + 29 * u);
 #pragma unroll
   for (int m = 0; m < M; ++m)
 #pragma unroll
@@ -67,10 +79,7 @@ __global__ void __launch_bounds__(kProbeThreads, 1)
 #pragma unroll
       for (int m = 0; m < M; ++m)
 #pragma unroll
-        for (int n = 0; n < 8; ++n)
-          // a different column operand in each of the 4 unrolled steps: with
-          // the same one, min(x, min(x, acc)) would fold to a single min
-          acc[m][n] = relax<T>(a[m], b[(n + u) & 7], acc[m][n]);
+        for (int n = 0; n < 8; ++n) acc[m][n] = relax<T>(a[m], b[u][n], acc[m][n]);
 #pragma unroll
     for (int m = 0; m < M; ++m) a[m] = acc[m][m];
   }
@@ -117,7 +126,7 @@ extern "C" fw_status fw_peak_probe(fw_dtype dtype, double* relax_per_s, double* 
     // the 64-bit pipes are far slower: fewer iterations for a similar duration
     const bool wide = dtype == FW_I64 || dtype == FW_F64;
     const int iters = wide ? 1 << 13 : 1 << 15;
-    const int chains = wide ? 32 : 64;
+    const int chains = wide ? 8 : 64;
     auto kern = dtype == FW_I32   ? k_probe<uint32_t>
                 : dtype == FW_F32 ? k_probe<float>
                 : dtype == FW_F64 ? k_probe<double>
