@@ -263,12 +263,30 @@ def bench_batched(fw, args):
             "timing": "events around fw_solve_batched (graph replay); inputs restored outside"}
 
 
+def _peaks():
+    """Measured copy bandwidth of the GB300s (driver-written), GB/s."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# Algorithmic bytes per (source i, vertex v) of the backward: the row kernel
+# reads dL/dD and pred and writes E; the column kernel reads pred and E and
+# writes dL/dW (4 bytes each).
+BWD_BYTES_PER_ENTRY = 24
+
+
 def bench_backward(fw, args):
     """64 digraphs, n = 1024, p = 0.1, fp32 weights in [1, 2): batched forward +
-    strided backward vs one forward and one backward launch per graph."""
+    strided backward through the C ABI, the same through FWFunction (the call a
+    training step makes; stored and recompute modes), and one forward and one
+    backward launch per graph."""
     import numpy as np
     import torch
     import graphgen.device as gdev
+    from paper_2403_18619_gb300.autograd import clear_plan_cache, shortest_paths
     B, n = 64, 1024
     W = torch.empty((B, n, n), dtype=torch.float32, device="cuda")
     for b in range(B):
@@ -286,7 +304,7 @@ def bench_backward(fw, args):
         plan.solve(Dl, Pl)
         fw.fw_backward_strided(G, D, P, GW)
     fw.fw_sync_status()
-    steps = max(2, args.steps)
+    steps = max(3, args.steps)
     f0, f1, b1 = _events(steps), _events(steps), _events(steps)
     for i in range(steps):
         D.copy_(W)
@@ -308,8 +326,41 @@ def bench_backward(fw, args):
     fw.fw_sync_status()
     t_single = a.elapsed_time(b)
     plan.close()
+
+    # the user's path: FWFunction forward (copy of W, batched solve) and backward
+    def autograd_ms(recompute):
+        Wt = W.detach().requires_grad_(True)
+        for _ in range(2):
+            Dt, _ = shortest_paths(Wt, recompute=recompute)
+            torch.autograd.backward(Dt, grad_tensors=G)
+            Wt.grad = None
+        ts = []
+        for _ in range(steps):
+            e0, e1 = _events(2)
+            e0.record()
+            Dt, _ = shortest_paths(Wt, recompute=recompute)
+            torch.autograd.backward(Dt, grad_tensors=G)
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+            Wt.grad = None
+            del Dt
+        return sum(ts) / len(ts)
+
+    ag = autograd_ms(False)
+    ag_rec = autograd_ms(True)
+    clear_plan_cache()
+    hbm, src = _peaks()
+    algo = float(B) * n * n * BWD_BYTES_PER_ENTRY
     return {"workload": "64 digraphs, n=1024, p=0.1, fp32 U[1,2), dL/dD ~ N(0,1)",
             "bwd_ms": bwd, "fwd_ms": fwd, "fwd_bwd_ms": fwd + bwd,
+            "bwd_roofline": {"bound": "hbm", "algorithmic_bytes": algo,
+                             "bytes_per_entry": BWD_BYTES_PER_ENTRY,
+                             "achieved_gbs": algo / (bwd * 1e-3) / 1e9, "peak_gbs": hbm,
+                             "frac": algo / (bwd * 1e-3) / 1e9 / hbm,
+                             "peak_source": "%s copy bandwidth" % src},
+            "autograd_fwd_bwd_ms": ag, "autograd_recompute_fwd_bwd_ms": ag_rec,
+            "autograd_over_raw": ag / (fwd + bwd),
             "one_launch_per_graph_fwd_bwd_ms": t_single,
             "speedup_vs_one_launch_per_graph": t_single / (fwd + bwd)}
 
@@ -317,30 +368,36 @@ def bench_backward(fw, args):
 def bench_configs(fw, args, only=None):
     """The other single-graph workloads: n = 1024 complete digraph, int32
     U[1,100], BS = 32 (launch / latency-bound), and n = 8192, p = 0.5, as fp32
-    (0,1] (with and without predecessors) and as int32 U[1,1000], each
-    against its own measured peak."""
+    (0,1] (with and without predecessors), int32 U[1,1000], fp64 (0,1] and
+    int64 U[1,1e12], each against its own measured peak (fw_peak_probe of its
+    dtype)."""
     import torch
     import graphgen.device as gdev
     out = {}
-    peaks = {fw.FW_I32: fw.fw_peak_probe(fw.FW_I32)[0], fw.FW_F32: fw.fw_peak_probe(fw.FW_F32)[0]}
     cases = [("n1024_i32_bs32", 1024, fw.FW_I32, 1.0, 32, dict(lo=1, hi=100), 1, True),
              ("n8192_i32_p0.5", 8192, fw.FW_I32, 0.5, 0, dict(lo=1, hi=1000), 2, True),
              ("n8192_f32_p0.5", 8192, fw.FW_F32, 0.5, 0, dict(kind=0), 2, True),
-             ("n8192_f32_p0.5_distance_only", 8192, fw.FW_F32, 0.5, 0, dict(kind=0), 2, False)]
+             ("n8192_f32_p0.5_distance_only", 8192, fw.FW_F32, 0.5, 0, dict(kind=0), 2, False),
+             ("n8192_f64_p0.5", 8192, fw.FW_F64, 0.5, 0, dict(kind=0), 2, True),
+             ("n8192_i64_p0.5", 8192, fw.FW_I64, 0.5, 0, dict(lo=1, hi=10 ** 12), 2, True)]
+    tdts = {fw.FW_I32: torch.int32, fw.FW_F32: torch.float32, fw.FW_I64: torch.int64,
+            fw.FW_F64: torch.float64}
+    fills = {fw.FW_I32: gdev.fill_i32, fw.FW_F32: gdev.fill_f32, fw.FW_I64: gdev.fill_i64,
+             fw.FW_F64: gdev.fill_f64}
+    peaks = {}
     for name, n, dt, p, bs, gen, seed, with_pred in cases:
         if only is not None and name != only:
             continue
+        if dt not in peaks:
+            peaks[dt] = fw.fw_peak_probe(dt)[0]
         ld = fw.padded(n)
-        tdt = torch.int32 if dt == fw.FW_I32 else torch.float32
-        W = torch.empty((n, ld), dtype=tdt, device="cuda")
-        if dt == fw.FW_I32:
-            gdev.fill_i32(W[:, :n], seed=seed, p=p, **gen)
-        else:
-            gdev.fill_f32(W[:, :n], seed=seed, p=p, **gen)
+        W = torch.empty((n, ld), dtype=tdts[dt], device="cuda")
+        fills[dt](W[:, :n], seed=seed, p=p, **gen)
         D = torch.empty_like(W)
         P = torch.empty((n, ld), dtype=torch.int32, device="cuda")
         opt = fw.Options.default(bs=bs)
-        steps = max(3, args.steps)
+        # the fp64 solve runs on GB300's narrow FP64 pipe (about 1 s at n = 8192)
+        steps = 3 if dt == fw.FW_F64 else max(3, args.steps)
         ts = []
         for i in range(2 + steps):
             D.copy_(W)
@@ -512,7 +569,8 @@ def main():
     ap.add_argument("--config", default=None,
                     help="time only this one of the other single-graph workloads "
                          "(n1024_i32_bs32, n8192_i32_p0.5, n8192_f32_p0.5, "
-                         "n8192_f32_p0.5_distance_only) and print its result, e.g. to profile it")
+                         "n8192_f32_p0.5_distance_only, n8192_f64_p0.5, n8192_i64_p0.5) and "
+                         "print its result, e.g. to profile it")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -343,8 +343,13 @@ fw_status solve_plan(fw_batched_plan* p, void* const* dist, int32_t* const* pred
   for (int64_t g = 0; g < p->batch && !changed; ++g)
     changed = dist[g] != p->cur_dist[g] || (void*)(pred ? pred[g] : nullptr) != p->cur_pred[g];
   if (changed) {
-    // new buffers: refresh the device tables, then re-record the graph
-    if (cudaStreamSynchronize(s) != cudaSuccess) return FW_ERR_CUDA;
+    // New buffers: refresh the device table of per-graph arguments, which the
+    // recorded kernels read when they run, with a copy ordered on s behind
+    // the previous solve.  Only a new status word (a solve on another stream)
+    // changes a kernel parameter of the recorded graph and needs a new
+    // recording, after that stream's earlier work.
+    const bool restream = st != p->cur_status;
+    if (restream && p->cur_status && cudaStreamSynchronize(s) != cudaSuccess) return FW_ERR_CUDA;
     A* ha = reinterpret_cast<A*>(p->h_args.data());
     for (int64_t g = 0; g < p->batch; ++g) {
       ha[g].D = reinterpret_cast<T*>(dist[g]);
@@ -354,16 +359,18 @@ fw_status solve_plan(fw_batched_plan* p, void* const* dist, int32_t* const* pred
       p->cur_pred[g] = ha[g].P;
     }
     p->cur_status = st;
-    if (cudaMemcpy(p->d_args, p->h_args.data(), p->h_args.size(), cudaMemcpyHostToDevice) !=
-        cudaSuccess)
+    if (cudaMemcpyAsync(p->d_args, p->h_args.data(), p->h_args.size(), cudaMemcpyHostToDevice,
+                        s) != cudaSuccess)
       return FW_ERR_CUDA;
-    if (p->exec) {
-      cudaGraphExecDestroy(p->exec);
-      p->exec = nullptr;
-    }
-    if (p->graph) {
-      cudaGraphDestroy(p->graph);
-      p->graph = nullptr;
+    if (restream) {
+      if (p->exec) {
+        cudaGraphExecDestroy(p->exec);
+        p->exec = nullptr;
+      }
+      if (p->graph) {
+        cudaGraphDestroy(p->graph);
+        p->graph = nullptr;
+      }
     }
   }
   if (!p->exec) {
