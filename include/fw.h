@@ -331,6 +331,58 @@ fw_status fw_solve_plan(int64_t n, const fw_options* opt, int32_t sms, int32_t* 
  */
 fw_status fw_queue_tasks(int32_t R, int64_t lookahead, int64_t first, int64_t count, int32_t* out);
 
+/*
+ * Tile-level calls of the blocked algorithm (Sec. 2.3, Fig. 2), for callers
+ * that keep a matrix in pieces -- the single-graph solve spread over several
+ * GPUs (2-D block-cyclic tiles, one exchange of pivot and panels per round;
+ * the exchange is the caller's).  All matrices are tile-PADDED: whole
+ * bs x bs tiles, padding vertices isolated (INF off the diagonal, 0 on it);
+ * pointers 16-byte aligned, leading dimensions multiples of 4, dtype as for
+ * fw_solve, bs 32, 64 or 128 (64-bit dtypes: 32 or 64).  Predecessors are
+ * last hops in global vertex ids; pred pointers may be NULL together (a
+ * distance-only solve).  Asynchronous on stream.
+ *
+ * fw_tile_closure: phase 1 -- the in-place strict-< FW closure of the
+ * bs x bs tile at `tile` (leading dimension ld) and its predecessors `pred`
+ * (same ld).  A negative diagonal entry is recorded in the stream's status
+ * word (fw_sync_status returns FW_ERR_NEG_CYCLE).
+ */
+fw_status fw_tile_closure(void* tile, int32_t* pred, int64_t ld, int32_t bs, fw_dtype dtype,
+                          void* stream);
+
+/*
+ * fw_tile_minplus: phases 2 to 4 -- for every output tile (i, j), 0 <= i <
+ * tiles_m, 0 <= j < tiles_n, of C (leading dimension ldc):
+ *     C_ij = min(C_ij, A_i (x) B_j),   (x) the min-plus product over bs steps,
+ * with A_i the bs x bs block (i, 0) of A (lda) and B_j the block (0, j) of B
+ * (ldb).  Where the entry strictly improves through step kk, Pc (leading
+ * dimension ldc) takes Pb[kk][column] (Pb: bs rows, leading dimension ldpb),
+ * the last hop of B's row kk.  With a closed pivot tile as A (row panel, B =
+ * C, Pb = Pc) or as B (column panel, A = C, Pb = the pivot's predecessors)
+ * this is the in-place panel update; with the column panel as A and the row
+ * panel as B it is the update of the remaining tiles.  C may be the same
+ * memory as A only when tiles_n == 1 and as B only when tiles_m == 1 (each
+ * output tile then reads exactly itself); any other overlap returns
+ * FW_ERR_ARG.  Tiles in tile row skip_tile_row or tile column skip_tile_col
+ * (-1: none) are not touched.  tiles_m <= 65535.
+ */
+fw_status fw_tile_minplus(void* C, int32_t* Pc, int64_t ldc, const void* A, int64_t lda,
+                          const void* B, int64_t ldb, const int32_t* Pb, int64_t ldpb,
+                          int64_t tiles_m, int64_t tiles_n, int32_t bs, int64_t skip_tile_row,
+                          int64_t skip_tile_col, fw_dtype dtype, void* stream);
+
+/*
+ * fw_block_init_pred: the initial predecessors (Sec. 2.3 leaves them open:
+ * the row's vertex on an edge, -1 elsewhere) of a rows x cols local block of
+ * a block-cyclic layout.  Local row a is global vertex (row_tile0 + (a / bs) *
+ * row_tile_step) * bs + a % bs, columns likewise; entries whose global row or
+ * column is >= n (padding) get -1.  dist and pred: leading dimension ld.
+ */
+fw_status fw_block_init_pred(const void* dist, int32_t* pred, int64_t ld, int64_t rows,
+                             int64_t cols, int32_t bs, int64_t n, int64_t row_tile0,
+                             int64_t row_tile_step, int64_t col_tile0, int64_t col_tile_step,
+                             fw_dtype dtype, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

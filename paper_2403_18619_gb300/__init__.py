@@ -18,7 +18,8 @@ __all__ = [
     "FWError", "Options", "load", "check", "fw_solve", "fw_solve_ex", "fw_solve_host",
     "fw_solve_noalloc", "fw_sync_status", "fw_backward", "fw_backward_strided",
     "fw_peak_probe", "fw_verify_certificate", "fw_release_workspace", "fw_solve_plan",
-    "fw_queue_tasks", "fw_paths", "BatchedPlan", "fw_bs_table", "fw_autotune_bs", "padded", "solve",
+    "fw_queue_tasks", "fw_paths", "fw_tile_closure", "fw_tile_minplus", "fw_block_init_pred",
+    "BatchedPlan", "fw_bs_table", "fw_autotune_bs", "padded", "solve",
     "solve_batched", "INF_I32", "INF_I64", "FW_I32", "FW_F32", "FW_I64", "FW_F64", "DRIVER_AUTO",
     "DRIVER_PERSISTENT", "DRIVER_PHASED",
 ]
@@ -106,6 +107,11 @@ def load():
         lib.fw_solve_plan.argtypes = [I64, P, I32, P, P, P, P]
         lib.fw_paths.argtypes = [P, I64, I64, P, P, I64, P, I64, P, P]
         lib.fw_solve_noalloc.argtypes = [P, P, I64, I64, I32, P]
+        lib.fw_tile_closure.argtypes = [P, P, I64, I32, I32, P]
+        lib.fw_tile_minplus.argtypes = [P, P, I64, P, I64, P, I64, P, I64, I64, I64, I32, I64,
+                                        I64, I32, P]
+        lib.fw_block_init_pred.argtypes = [P, P, I64, I64, I64, I32, I64, I64, I64, I64, I64,
+                                           I32, P]
         lib.fw_bs_table.argtypes = [P, I32]
         lib.fw_autotune_bs.argtypes = [I32, I64, I64, P, P, P]
         for name in ("fw_solve", "fw_solve_ex", "fw_solve_host", "fw_batched_plan_create",
@@ -113,7 +119,8 @@ def load():
                      "fw_backward", "fw_backward_strided", "fw_sync_status",
                      "fw_release_workspace", "fw_peak_probe", "fw_verify_certificate",
                      "fw_queue_tasks", "fw_solve_noalloc", "fw_bs_table", "fw_autotune_bs",
-                     "fw_solve_plan", "fw_paths"):
+                     "fw_solve_plan", "fw_paths", "fw_tile_closure", "fw_tile_minplus",
+                     "fw_block_init_pred"):
             getattr(lib, name).restype = I32
         _lib = lib
         return lib
@@ -305,6 +312,70 @@ def fw_queue_tasks(R: int, lookahead: int, first: int = 0, count: int | None = N
     out = np.zeros((count, 4), np.int32)
     check(load().fw_queue_tasks(R, lookahead, first, count, out.ctypes.data), "fw_queue_tasks")
     return out
+
+
+def _block(t, name):
+    """(pointer, rows, cols, ld) of a CUDA 2-D tensor with unit column stride."""
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if t.dim() != 2 or t.stride(1) != 1:
+        raise ValueError("%s must be a 2-D view with unit column stride" % name)
+    return t.data_ptr(), t.shape[0], t.shape[1], t.stride(0)
+
+
+def fw_tile_closure(tile, pred, bs: int, stream=None) -> None:
+    """fw_tile_closure on a bs x bs CUDA view (pred: same layout, or None)."""
+    tp, r, c, ld = _block(tile, "tile")
+    if r != bs or c != bs:
+        raise ValueError("tile must be bs x bs")
+    pp = None
+    if pred is not None:
+        pp, r2, c2, ld2 = _block(pred, "pred")
+        if (r2, c2, ld2) != (r, c, ld):
+            raise ValueError("pred must have the tile's shape and row stride")
+    check(load().fw_tile_closure(tp, pp, ld, bs, _dtype_code(tile), _stream_ptr(stream)),
+          "fw_tile_closure")
+
+
+def fw_tile_minplus(C, Pc, A, B, Pb, bs: int, skip_tile_row: int = -1, skip_tile_col: int = -1,
+                    stream=None) -> None:
+    """fw_tile_minplus: C = min(C, A (x) B) tile by tile, Pc from Pb's rows
+    (Pc, Pb: None for distances only).  C is (tiles_m * bs) x (tiles_n * bs);
+    A is (tiles_m * bs) x bs, B and Pb are bs x (tiles_n * bs)."""
+    cp, cr, cc, ldc = _block(C, "C")
+    ap, ar, ac, lda = _block(A, "A")
+    bp, br, bc, ldb = _block(B, "B")
+    if cr % bs or cc % bs or ar != cr or ac != bs or br != bs or bc != cc:
+        raise ValueError("shapes must be C (m bs x n bs), A (m bs x bs), B (bs x n bs)")
+    if A.dtype != C.dtype or B.dtype != C.dtype:
+        raise TypeError("A, B and C must share a dtype")
+    pcp = pbp = None
+    ldpb = 0
+    if (Pc is None) != (Pb is None):
+        raise ValueError("Pc and Pb must both be given or both be None")
+    if Pc is not None:
+        pcp, r2, c2, ld2 = _block(Pc, "Pc")
+        if (r2, c2, ld2) != (cr, cc, ldc):
+            raise ValueError("Pc must have C's shape and row stride")
+        pbp, r3, c3, ldpb = _block(Pb, "Pb")
+        if (r3, c3) != (bs, cc):
+            raise ValueError("Pb must be bs x (tiles_n * bs)")
+    check(load().fw_tile_minplus(cp, pcp, ldc, ap, lda, bp, ldb, pbp, ldpb, cr // bs, cc // bs,
+                                 bs, skip_tile_row, skip_tile_col, _dtype_code(C),
+                                 _stream_ptr(stream)), "fw_tile_minplus")
+
+
+def fw_block_init_pred(dist, pred, bs: int, n: int, row_tile0: int, row_tile_step: int,
+                       col_tile0: int, col_tile_step: int, stream=None) -> None:
+    """fw_block_init_pred on a local block (CUDA views with one row stride)."""
+    dp, r, c, ld = _block(dist, "dist")
+    pp, r2, c2, ld2 = _block(pred, "pred")
+    if (r2, c2, ld2) != (r, c, ld):
+        raise ValueError("pred must have dist's shape and row stride")
+    check(load().fw_block_init_pred(dp, pp, ld, r, c, bs, n, row_tile0, row_tile_step,
+                                    col_tile0, col_tile_step, _dtype_code(dist),
+                                    _stream_ptr(stream)), "fw_block_init_pred")
 
 
 class BatchedPlan:

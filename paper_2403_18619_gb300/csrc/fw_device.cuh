@@ -944,24 +944,18 @@ __device__ __forceinline__ void pivot_packed(const Args<T>& a, int r, void* smem
   }
 }
 
-// Eager pivot: compare and select per relaxation (fp32, large int32 entries).
+// The BS steps of the in-place FW closure of one tile held as micro-tiles
+// (d, p) by the 256 compute threads: step kk broadcasts row kk and column kk
+// through shared memory (double-buffered, one barrier per step) and relaxes
+// every owned element through kk with a strict-< compare, the last hop taken
+// from row kk's predecessors.  Shared memory: 2 * BS * (2 * sizeof(T) + 4) bytes.
 template <typename T, int BS>
-__device__ __noinline__ void pivot_eager(const Args<T>& a, int r, void* smem_raw) {
+__device__ __forceinline__ void closure_steps(T (&d)[Geo<BS>::TM][Geo<BS>::TM],
+                                              int32_t (&p)[Geo<BS>::TM][Geo<BS>::TM],
+                                              void* smem_raw) {
   using Gm = Geo<BS>;
   constexpr int TM = Gm::TM, G = Gm::G;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  T d[TM][TM];
-  int32_t p[TM][TM];
-  load_tile<BS>(d, a.D, a.n, a.ld, r, r, tx, ty, Num<T>::inf());
-  if (a.P) {
-    load_tile<BS>(p, a.P, a.n, a.ld, r, r, tx, ty, (int32_t)-1);
-  } else {
-#pragma unroll
-    for (int mm = 0; mm < TM; ++mm)
-#pragma unroll
-      for (int nn = 0; nn < TM; ++nn) p[mm][nn] = -1;
-  }
-  stamp(1);
   T* rowD = reinterpret_cast<T*>(smem_raw);  // [2][BS]
   int32_t* rowP = reinterpret_cast<int32_t*>(rowD + 2 * BS);
   T* colD = reinterpret_cast<T*>(rowP + 2 * BS);
@@ -1006,6 +1000,28 @@ __device__ __noinline__ void pivot_eager(const Args<T>& a, int r, void* smem_raw
       }
     }
   }
+}
+
+// Eager pivot: compare and select per relaxation (fp32, 64-bit types, large
+// int32 entries).
+template <typename T, int BS>
+__device__ __noinline__ void pivot_eager(const Args<T>& a, int r, void* smem_raw) {
+  using Gm = Geo<BS>;
+  constexpr int TM = Gm::TM;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  T d[TM][TM];
+  int32_t p[TM][TM];
+  load_tile<BS>(d, a.D, a.n, a.ld, r, r, tx, ty, Num<T>::inf());
+  if (a.P) {
+    load_tile<BS>(p, a.P, a.n, a.ld, r, r, tx, ty, (int32_t)-1);
+  } else {
+#pragma unroll
+    for (int mm = 0; mm < TM; ++mm)
+#pragma unroll
+      for (int nn = 0; nn < TM; ++nn) p[mm][nn] = -1;
+  }
+  stamp(1);
+  closure_steps<T, BS>(d, p, smem_raw);
   stamp(2);
   stamp(3);
   pivot_store_dist<T, BS>(a, r, d, tx, ty);

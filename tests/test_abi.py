@@ -183,3 +183,38 @@ def test_paths_argument_checks(fw):
     assert lib.fw_paths(p, 10, 10, p, p, -1, p, 4, p, None) == 1
     assert lib.fw_paths(p, 10, 10, p, p, 1, p, 0, p, None) == 1
     assert lib.fw_paths(p, 10, 10, p, p, 0, p, 4, p, None) == 0
+
+
+def test_wide_dtype_and_tile_call_host_checks(fw):
+    """Checks made on the host before any CUDA call: 64-bit dtypes take BS 32
+    or 64, and the tile-level calls reject bad block sizes, dtypes, leading
+    dimensions, misalignment and the overlaps they do not allow."""
+    lib = fw.load()
+    g = 0x10000  # never dereferenced
+    o = fw.Options.default(bs=128)
+    for dt in (fw.FW_I64, fw.FW_F64):
+        assert lib.fw_solve_ex(g, g + 4096, 8, 8, dt, ctypes.byref(o), None) == 6
+    # fw_tile_closure
+    assert lib.fw_tile_closure(g, g + 65536, 64, 48, fw.FW_I32, None) == 1     # bs
+    assert lib.fw_tile_closure(g, g + 65536, 64, 64, 9, None) == 1             # dtype
+    assert lib.fw_tile_closure(g, g + 65536, 32, 64, fw.FW_I32, None) == 1     # ld < bs
+    assert lib.fw_tile_closure(g + 4, g + 65536, 64, 64, fw.FW_I32, None) == 1  # misaligned
+    assert lib.fw_tile_closure(g, g, 64, 64, fw.FW_I32, None) == 1              # pred == dist
+    assert lib.fw_tile_closure(g, g + 65536, 128, 128, fw.FW_F64, None) == 6   # 64-bit bs 128
+    # fw_tile_minplus(C, Pc, ldc, A, lda, B, ldb, Pb, ldpb, tm, tn, bs, si, sj, dtype, s)
+    M = lib.fw_tile_minplus
+    A, B, C, Pc, Pb = g, g + (1 << 20), g + (2 << 20), g + (3 << 20), g + (4 << 20)
+    I32 = fw.FW_I32
+    assert M(C, Pc, 128, A, 32, B, 128, None, 128, 2, 4, 32, -1, -1, I32, None) == 1  # Pb missing
+    assert M(C, Pc, 64, A, 32, B, 128, Pb, 128, 2, 4, 32, -1, -1, I32, None) == 1     # ldc < 4 bs
+    assert M(C, Pc, 128, A, 32, B, 128, Pb, 128, 2, 4, 48, -1, -1, I32, None) == 1    # bs
+    assert M(C, Pc, 130, A, 32, B, 128, Pb, 128, 2, 4, 32, -1, -1, I32, None) == 1    # ld % 4
+    assert M(C + 8, Pc, 128, A, 32, B, 128, Pb, 128, 2, 4, 32, -1, -1, I32, None) == 1  # align
+    # C may be A only with one tile column, B only with one tile row
+    assert M(C, Pc, 128, C, 128, B, 128, Pb, 128, 2, 4, 32, -1, -1, I32, None) == 1
+    assert M(C, Pc, 128, A, 32, C, 128, Pb, 128, 2, 4, 32, -1, -1, I32, None) == 1
+    assert M(C, Pc, 128, A, 32, B, 128, Pc, 128, 2, 4, 32, -1, -1, I32, None) == 1
+    assert M(C, Pc, 128, A, 32, B, 128, Pb, 128, 0, 4, 32, -1, -1, I32, None) == 0    # no tiles
+    assert M(C, Pc, 128, A, 32, B, 128, Pb, 128, 2, 4, 128, -1, -1, fw.FW_F64, None) == 6
+    assert lib.fw_block_init_pred(None, g, 8, 8, 8, 32, 8, 0, 1, 0, 1, I32, None) == 1
+    assert lib.fw_block_init_pred(g, g + 4096, 8, 0, 8, 32, 8, 0, 1, 0, 1, I32, None) == 0
