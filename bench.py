@@ -200,15 +200,13 @@ def _events(k):
     return [torch.cuda.Event(enable_timing=True) for _ in range(k)]
 
 
-def bench_batched(fw, args):
-    """512 digraphs, n uniform in [64, 2048], p = 0.3, int32 weights in [1, 100]:
-    one batched launch (CUDA-graph replay) vs one fw_solve launch per graph."""
-    import numpy as np
+def _batched_inputs(fw):
+    """The 512-graph workload: n uniform in [64, 2048] (seed 11), p = 0.3,
+    int32 weights in [1, 100]; inputs W and output buffers D, P per graph."""
     import torch
     import graphgen
     import graphgen.device as gdev
     ns = graphgen.batch_sizes(11, 512, 64, 2048)
-    table, tune_ms = fw.fw_autotune_bs(fw.FW_I32, graphs_per_class=16, max_n=2048)
     W, D, P = [], [], []
     for b, n in enumerate(ns):
         n = int(n)
@@ -218,6 +216,48 @@ def bench_batched(fw, args):
         W.append(w)
         D.append(torch.empty_like(w))
         P.append(torch.empty_like(w))
+    return ns, W, D, P
+
+
+def trace_batched(fw, out_path):
+    """One traced batched solve of the 512-graph workload (autotuned block
+    sizes, every task traced): writes tracing.summarize_batched as JSON."""
+    import torch
+    from paper_2403_18619_gb300 import tracing
+    fw.fw_autotune_bs(fw.FW_I32, graphs_per_class=16, max_n=2048)
+    ns, W, D, P = _batched_inputs(fw)
+    lds = [fw.padded(int(n)) for n in ns]
+    probe = fw.BatchedPlan([int(n) for n in ns], lds, fw.FW_I32)
+    bsv, ntasks = probe.info()
+    probe.close()
+    tr = torch.zeros((ntasks, 10), dtype=torch.int64, device="cuda")
+    opt = fw.Options.default(trace=tr.data_ptr(), trace_cap=ntasks, trace_stride=1)
+    plan = fw.BatchedPlan([int(n) for n in ns], lds, fw.FW_I32, opt)
+    Dv = [d[:, :int(n)] for d, n in zip(D, ns)]
+    Pv = [p_[:, :int(n)] for p_, n in zip(P, ns)]
+    for _ in range(2):  # the second solve is the one kept (warm)
+        for d, w in zip(D, W):
+            d.copy_(w)
+        tr.zero_()
+        plan.solve(Dv, Pv)
+        fw.fw_sync_status()
+    plan.close()
+    s = tracing.summarize_batched(tr.cpu().numpy(), [int(n) for n in ns], bsv.tolist())
+    s["workload"] = "512 digraphs, n ~ U[64,2048] (seed 11), p=0.3, int32 U[1,100]"
+    s["bs_table"] = fw.fw_bs_table().tolist()
+    with open(out_path, "w") as f:
+        json.dump(s, f, indent=1)
+    print(json.dumps({"trace_summary": out_path, "tasks": s.get("tasks"),
+                      "busy_fraction": s.get("busy_fraction")}), flush=True)
+
+
+def bench_batched(fw, args):
+    """512 digraphs, n uniform in [64, 2048], p = 0.3, int32 weights in [1, 100]:
+    one batched launch (CUDA-graph replay) vs one fw_solve launch per graph."""
+    import numpy as np
+    import torch
+    table, tune_ms = fw.fw_autotune_bs(fw.FW_I32, graphs_per_class=16, max_n=2048)
+    ns, W, D, P = _batched_inputs(fw)
     plan = fw.BatchedPlan([int(n) for n in ns], [fw.padded(int(n)) for n in ns], fw.FW_I32)
     bsv, ntasks = plan.info()
     Dv = [d[:, :int(n)] for d, n in zip(D, ns)]
@@ -255,8 +295,10 @@ def bench_batched(fw, args):
     t_single = a.elapsed_time(b)
     plan.close()
     relax = float(sum(int(n) ** 3 for n in ns))
+    peak = fw.fw_peak_probe(fw.FW_I32)[0]
     return {"workload": "512 digraphs, n ~ U[64,2048] (seed 11), p=0.3, int32 U[1,100]",
             "graphs_per_s": 512 / (t_batched * 1e-3), "relax_per_s": relax / (t_batched * 1e-3),
+            "frac_of_peak": relax / (t_batched * 1e-3) / peak, "peak_relax_per_s": peak,
             "ms": t_batched, "one_launch_per_graph_ms": t_single,
             "speedup_vs_one_launch_per_graph": t_single / t_batched,
             "bs_table": table.tolist(), "tasks": int(ntasks),
@@ -365,6 +407,64 @@ def bench_backward(fw, args):
             "speedup_vs_one_launch_per_graph": t_single / (fwd + bwd)}
 
 
+def _single_configs(fw):
+    """(name, n, dtype, edge p, BS (0: automatic), generator arguments, seed,
+    with predecessors) of the single-graph workloads besides the headline."""
+    return [("n1024_i32_bs32", 1024, fw.FW_I32, 1.0, 32, dict(lo=1, hi=100), 1, True),
+            ("n8192_i32_p0.5", 8192, fw.FW_I32, 0.5, 0, dict(lo=1, hi=1000), 2, True),
+            ("n8192_f32_p0.5", 8192, fw.FW_F32, 0.5, 0, dict(kind=0), 2, True),
+            ("n8192_f32_p0.5_distance_only", 8192, fw.FW_F32, 0.5, 0, dict(kind=0), 2, False),
+            ("n8192_f64_p0.5", 8192, fw.FW_F64, 0.5, 0, dict(kind=0), 2, True),
+            ("n8192_i64_p0.5", 8192, fw.FW_I64, 0.5, 0, dict(lo=1, hi=10 ** 12), 2, True)]
+
+
+def _torch_dtype(fw, dt):
+    import torch
+    return {fw.FW_I32: torch.int32, fw.FW_F32: torch.float32, fw.FW_I64: torch.int64,
+            fw.FW_F64: torch.float64}[dt]
+
+
+def _fill(fw, dt):
+    import graphgen.device as gdev
+    return {fw.FW_I32: gdev.fill_i32, fw.FW_F32: gdev.fill_f32, fw.FW_I64: gdev.fill_i64,
+            fw.FW_F64: gdev.fill_f64}[dt]
+
+
+def trace_config(fw, name, out_path):
+    """One traced solve (every task) of a single-graph workload of bench_configs:
+    writes tracing.summarize and tracing.critical_path as JSON."""
+    import torch
+    import graphgen.device as gdev
+    from paper_2403_18619_gb300 import tracing
+    spec = {c[0]: c for c in _single_configs(fw)}.get(name)
+    if spec is None:
+        raise SystemExit("unknown config %r" % name)
+    _, n, dt, p, bs, gen, seed, with_pred = spec
+    ld = fw.padded(n)
+    W = torch.empty((n, ld), dtype=_torch_dtype(fw, dt), device="cuda")
+    _fill(fw, dt)(W[:, :n], seed=seed, p=p, **gen)
+    D = torch.empty_like(W)
+    P = torch.empty((n, ld), dtype=torch.int32, device="cuda")
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    plan = fw.fw_solve_plan(n, fw.Options.default(bs=bs), sms)
+    R, look = plan["rounds"], plan["lookahead"]
+    tr = torch.zeros((R ** 3, 10), dtype=torch.int64, device="cuda")
+    opt = fw.Options.default(bs=bs, trace=tr.data_ptr(), trace_cap=R ** 3, trace_stride=1)
+    for _ in range(3):  # the last solve is the one kept (warm)
+        D.copy_(W)
+        tr.zero_()
+        fw.fw_solve_ex(D[:, :n], P[:, :n] if with_pred else None, opt)
+        fw.fw_sync_status()
+    t = tr.cpu().numpy()
+    out = {"config": name, "n": n, "bs": plan["bs"], "rounds": R, "lookahead": look,
+           "summary": tracing.summarize(t),
+           "critical_path": tracing.critical_path(t, fw.fw_queue_tasks(R, look))}
+    with open(out_path, "w") as f:
+        json.dump(out, f, indent=1)
+    print(json.dumps({"trace": out_path, "round_us": out["critical_path"].get("round_us")}),
+          flush=True)
+
+
 def bench_configs(fw, args, only=None):
     """The other single-graph workloads: n = 1024 complete digraph, int32
     U[1,100], BS = 32 (launch / latency-bound), and n = 8192, p = 0.5, as fp32
@@ -374,25 +474,15 @@ def bench_configs(fw, args, only=None):
     import torch
     import graphgen.device as gdev
     out = {}
-    cases = [("n1024_i32_bs32", 1024, fw.FW_I32, 1.0, 32, dict(lo=1, hi=100), 1, True),
-             ("n8192_i32_p0.5", 8192, fw.FW_I32, 0.5, 0, dict(lo=1, hi=1000), 2, True),
-             ("n8192_f32_p0.5", 8192, fw.FW_F32, 0.5, 0, dict(kind=0), 2, True),
-             ("n8192_f32_p0.5_distance_only", 8192, fw.FW_F32, 0.5, 0, dict(kind=0), 2, False),
-             ("n8192_f64_p0.5", 8192, fw.FW_F64, 0.5, 0, dict(kind=0), 2, True),
-             ("n8192_i64_p0.5", 8192, fw.FW_I64, 0.5, 0, dict(lo=1, hi=10 ** 12), 2, True)]
-    tdts = {fw.FW_I32: torch.int32, fw.FW_F32: torch.float32, fw.FW_I64: torch.int64,
-            fw.FW_F64: torch.float64}
-    fills = {fw.FW_I32: gdev.fill_i32, fw.FW_F32: gdev.fill_f32, fw.FW_I64: gdev.fill_i64,
-             fw.FW_F64: gdev.fill_f64}
     peaks = {}
-    for name, n, dt, p, bs, gen, seed, with_pred in cases:
+    for name, n, dt, p, bs, gen, seed, with_pred in _single_configs(fw):
         if only is not None and name != only:
             continue
         if dt not in peaks:
             peaks[dt] = fw.fw_peak_probe(dt)[0]
         ld = fw.padded(n)
-        W = torch.empty((n, ld), dtype=tdts[dt], device="cuda")
-        fills[dt](W[:, :n], seed=seed, p=p, **gen)
+        W = torch.empty((n, ld), dtype=_torch_dtype(fw, dt), device="cuda")
+        _fill(fw, dt)(W[:, :n], seed=seed, p=p, **gen)
         D = torch.empty_like(W)
         P = torch.empty((n, ld), dtype=torch.int32, device="cuda")
         opt = fw.Options.default(bs=bs)
@@ -571,9 +661,27 @@ def main():
                          "(n1024_i32_bs32, n8192_i32_p0.5, n8192_f32_p0.5, "
                          "n8192_f32_p0.5_distance_only, n8192_f64_p0.5, n8192_i64_p0.5) and "
                          "print its result, e.g. to profile it")
+    ap.add_argument("--trace-config", nargs=2, default=None, metavar=("NAME", "OUT.json"),
+                    help="trace one solve of a single-graph workload (as --config) and write "
+                         "the trace summary and its per-round critical path")
+    ap.add_argument("--trace-batched", default=None, metavar="OUT.json",
+                    help="trace one batched solve of the 512-graph workload and write its "
+                         "summary by size class (no timing line)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.trace_config:
+        import torch
+        import paper_2403_18619_gb300 as fw
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        trace_config(fw, args.trace_config[0], args.trace_config[1])
+        return 0
+    if args.trace_batched:
+        import torch
+        import paper_2403_18619_gb300 as fw
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        trace_batched(fw, args.trace_batched)
+        return 0
     if args.config:
         import torch
         import paper_2403_18619_gb300 as fw

@@ -167,6 +167,10 @@ fw_status fw_solve_host(void* dist_host, int32_t* pred_host, int64_t n, int64_t 
  *   n[b], ld[b]  vertex count and leading dimension of graph b (same rules as
  *                fw_solve), 0 <= b < batch, 1 <= batch <= 65536.
  *   opt->bs      0 = per-size-class choice (autotuned table), else a fixed BS.
+ *   opt->trace   optional task trace of every solve with this plan (as for
+ *                fw_solve_ex; the global task index is the position in the
+ *                plan's interleaved list, and word 0 also carries the graph
+ *                index in bits 40-63).
  */
 typedef struct fw_batched_plan fw_batched_plan;
 

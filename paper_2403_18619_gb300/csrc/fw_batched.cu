@@ -33,6 +33,8 @@ struct BatchParams {
   int* status;
   int* abort_flag;
   int64_t timeout_ns;
+  uint64_t* trace;  // optional per-task trace (fw_options.trace of the plan)
+  int trace_cap, trace_stride;
 };
 
 template <typename T>
@@ -50,7 +52,8 @@ struct BatchSrc {
   int trace_cap = 0, trace_stride = 0;
   __device__ explicit BatchSrc(const BatchParams<T>& p)
       : graphs(p.graphs), bsv(p.bsv), list(p.list), ntasks(p.ntasks), next(p.next),
-        status(p.status), abort_flag(p.abort_flag), timeout_ns(p.timeout_ns) {}
+        status(p.status), abort_flag(p.abort_flag), timeout_ns(p.timeout_ns), trace(p.trace),
+        trace_cap(p.trace_cap), trace_stride(p.trace_stride) {}
   __device__ int64_t total() const { return ntasks; }
   __device__ fwh::Task resolve(int64_t t, int& g) const {
     const uint2 e = list[t];
@@ -311,6 +314,9 @@ cudaError_t enqueue(fw_batched_plan* p, cudaStream_t s) {
   bp.status = p->cur_status;
   bp.abort_flag = p->d_abort;
   bp.timeout_ns = p->opt.timeout_ns > 0 ? p->opt.timeout_ns : 2000000000LL;
+  bp.trace = p->opt.trace;
+  bp.trace_cap = (int)p->opt.trace_cap;
+  bp.trace_stride = p->opt.trace_stride;
   cudaLaunchConfig_t lc{};
   lc.gridDim = dim3((unsigned)p->grid);
   lc.blockDim = dim3(fwk::kWsThreads);
@@ -452,6 +458,8 @@ fw_status fw_batched_plan_create(fw_batched_plan** plan, const int64_t* n, const
   fw_options_default(&o);
   if (opt) o = *opt;
   if (o.bs != 0 && o.bs != 32 && o.bs != 64 && o.bs != 128) return FW_ERR_ARG;
+  if (o.trace && (o.trace_cap <= 0 || o.trace_cap > (1 << 30) || o.trace_stride <= 0))
+    return FW_ERR_ARG;
   for (int64_t g = 0; g < batch; ++g)
     if (n[g] < 1 || n[g] > 131072 || ld[g] < n[g] || (ld[g] % 4) != 0) return FW_ERR_ARG;
   auto* p = new fw_batched_plan();

@@ -82,9 +82,13 @@ struct WsBars {
 };
 
 // Bounded wait on an mbarrier phase; false (and the timeout status) on expiry.
-// With poll_abort it also gives up, without recording anything, once another
-// CTA has raised the abort flag, so that one failure does not make every
-// pending wait of every CTA run out its own limit in turn.
+// With poll_abort, a wait that has already lasted over a millisecond (normal
+// waits take microseconds) also gives up, without recording anything, once
+// another CTA has raised the abort flag, so that one failure does not make
+// every pending wait of every CTA run out its own limit in turn.  Polling the
+// flag from the start cost the compute warps' operand waits about 1 % of the
+// n = 32768 solve.
+constexpr uint64_t kAbortPollAfterNs = 1000000;
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, int* status,
                                           int* abort_flag, int64_t timeout_ns,
                                           bool poll_abort = true) {
@@ -93,8 +97,9 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, int* s
   for (int64_t it = 0; it < ((int64_t)1 << 26); ++it) {
     if (mbar_try_wait_sleep(bar, parity, 20000u)) return true;
     if ((it & 15) == 15) {
-      if (poll_abort && ld_relaxed(abort_flag)) return false;
-      if (globaltimer() - t0 > (uint64_t)timeout_ns) break;
+      const uint64_t waited = globaltimer() - t0;
+      if (waited > (uint64_t)timeout_ns) break;
+      if (poll_abort && waited > kAbortPollAfterNs && ld_relaxed(abort_flag)) return false;
     }
   }
   atomicOr(status, kStTimeout);
@@ -619,7 +624,7 @@ __device__ void issue_operands(const Args<T>& a, const fwh::Task& k, bool fast, 
 }
 
 // Optional per-task trace (sampled tasks): 10 words per entry.
-//   [0] task | type << 32   [1] SM id
+//   [0] task | type << 32 | graph << 40   [1] SM id
 //   producer: [2] claimed  [3] inputs ready  [4] copies issued  [5] published
 //   compute : [6] descriptor seen  [9] task finished (stores issued)
 //   min-plus tasks: [7], [8] SM-cycle counts of the task's phases
@@ -780,7 +785,7 @@ __device__ void ws_engine(const Src& src, unsigned char* smem, WsBars& wb, CtaSc
       }
       if (lane == 0) {
         if (uint64_t* tr = trace_slot(src.trace, src.trace_cap, src.trace_stride, t)) {
-          tr[0] = (uint64_t)(unsigned)t | ((uint64_t)k.type << 32);
+          tr[0] = (uint64_t)(unsigned)t | ((uint64_t)k.type << 32) | ((uint64_t)(unsigned)g << 40);
           tr[4] = globaltimer();
         }
       }

@@ -6,7 +6,8 @@ claimed, when its inputs were ready, when its operands were issued, when the
 compute warps started and finished it, and when it was published.  The buffer
 (``trace_cap`` rows of 10 uint64, filled on the device; include/fw.h) holds:
 
-  [0] task index | type << 32   (0 pivot, 1 row panel, 2 column panel, 3 remaining tile)
+  [0] task index | type << 32 | graph << 40   (type: 0 pivot, 1 row panel,
+      2 column panel, 3 remaining tile; graph: the graph of a batched solve)
   [1] SM id
   [2] claimed  [3] inputs ready  [4] operands issued  [5] published   (%globaltimer, ns)
   [6] compute start  [9] compute end                                  (%globaltimer, ns)
@@ -37,6 +38,7 @@ def decode(trace) -> dict:
     return {
         "task": (t[:, 0] & m32).astype(np.int64),
         "type": ((t[:, 0] >> np.uint64(32)) & np.uint64(0xFF)).astype(np.int64),
+        "graph": (t[:, 0] >> np.uint64(40)).astype(np.int64),
         "sm": t[:, 1].astype(np.int64),
         "claimed": t[:, 2].astype(np.int64),
         "ready": t[:, 3].astype(np.int64),
@@ -117,4 +119,92 @@ def summarize(trace) -> dict:
     out["busy_fraction"] = {"mean": float(np.mean(busy)), "min": float(np.min(busy)),
                             "sms": len(busy)}
     out["gap_us"] = _stats(np.concatenate(gaps) if gaps else np.zeros(0))
+    return out
+
+
+def summarize_batched(trace, ns, bs_per_graph, bounds=(128, 256, 512, 1024, 2048)) -> dict:
+    """A batched solve's trace by size class of the graphs (n <= bound): per
+    class and task type the tasks, the mean compute time and the mean wait for
+    inputs (claim to ready, microseconds), the class's share of the compute
+    time, and the span from its first claim to its last publication; overall,
+    the busy fraction of the compute warps and the share of compute time per
+    task type.  ns, bs_per_graph: vertex count and block size of every graph."""
+    d = decode(trace)
+    out = summarize(trace)
+    if d["task"].size == 0:
+        return out
+    ns = np.asarray(ns, np.int64)
+    bsg = np.asarray(bs_per_graph, np.int64)
+    cls = np.searchsorted(np.asarray(bounds), ns[d["graph"]], side="left")
+    comp = (d["end"] - d["start"]).astype(np.float64) / 1e3
+    wait = (d["ready"] - d["claimed"]).astype(np.float64) / 1e3
+    total = comp.sum()
+    out["compute_share_by_type"] = {TYPES[t]: float(comp[d["type"] == t].sum() / total)
+                                    for t in range(4) if (d["type"] == t).any()}
+    by = {}
+    for c in np.unique(cls):
+        m = cls == c
+        name = "n<=%d" % bounds[c] if c < len(bounds) else "n>%d" % bounds[-1]
+        g = np.unique(d["graph"][m])
+        e = {"graphs": int(g.size), "bs": sorted(set(int(x) for x in bsg[g])),
+             "compute_share": float(comp[m].sum() / total),
+             "span_us": float((d["published"][m].max() - d["claimed"][m].min()) / 1e3)}
+        for t in range(4):
+            mt = m & (d["type"] == t)
+            if mt.any():
+                e[TYPES[t]] = {"tasks": int(mt.sum()), "compute_us": float(comp[mt].mean()),
+                               "input_wait_us": float(wait[mt].mean())}
+        by[name] = e
+    out["by_class"] = by
+    return out
+
+
+CHAIN = ("pivot", "row_panel", "col_panel", "remaining")
+
+
+def critical_path(trace, queue) -> dict:
+    """Per-round breakdown of the chain that bounds a solve with few tiles:
+    pivot(r) -> panels (r, r+1) and (r+1, r) -> remaining tile (r+1, r+1) of
+    round r -> pivot(r+1) (Sec. 2.3: the next round's pivot tile is the last
+    tile round r updates on its path).  queue: the solve's task list, one row
+    (type, round, tile row, tile column) per task index (fw_queue_tasks).  For
+    every round with all five tasks traced, the segments (microseconds, means
+    over rounds):
+      pivot      compute of pivot(r)      pivot_pub  its publication
+      to_panels  publication to the later panel's compute start
+      panels     the two panels' compute (to the later end)
+      panel_pub  their publication
+      to_tile    to the remaining tile's compute start
+      tile       its compute          tile_pub   its publication
+      to_pivot   to pivot(r+1)'s compute start
+    and their sum, the round time along the chain."""
+    d = decode(trace)
+    q = np.asarray(queue)
+    key = {(int(t), int(r), int(i), int(j)): k for k, (t, r, i, j) in enumerate(q)}
+    row = {int(t): k for k, t in enumerate(d["task"])}
+
+    def get(typ, r, i, j):
+        k = key.get((typ, r, i, j))
+        return row.get(k) if k is not None else None
+
+    names = ("pivot", "pivot_pub", "to_panels", "panels", "panel_pub", "to_tile", "tile",
+             "tile_pub", "to_pivot")
+    segs = {k: [] for k in names}
+    R = int(q[:, 1].max()) + 1 if len(q) else 0
+    for r in range(R - 1):
+        ids = [get(0, r, r, r), get(1, r, r, r + 1), get(2, r, r + 1, r), get(3, r, r + 1, r + 1),
+               get(0, r + 1, r + 1, r + 1)]
+        if any(x is None for x in ids):
+            continue
+        pv, prow, pcol, tl, nx = ids
+        st, en, pb = d["start"], d["end"], d["published"]
+        t = [st[pv], en[pv], pb[pv], max(st[prow], st[pcol]), max(en[prow], en[pcol]),
+             max(pb[prow], pb[pcol]), st[tl], en[tl], pb[tl], st[nx]]
+        for k, a, b in zip(names, t[:-1], t[1:]):
+            segs[k].append((b - a) / 1e3)
+    out = {"rounds": len(segs["pivot"])}
+    if out["rounds"]:
+        means = {k: float(np.mean(v)) for k, v in segs.items()}
+        out["segments_us"] = means
+        out["round_us"] = float(sum(means.values()))
     return out

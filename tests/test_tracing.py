@@ -64,3 +64,54 @@ def test_empty_and_bad_shapes():
     assert tracing.summarize(np.zeros((4, 10), np.uint64)) == {"tasks": 0}
     with pytest.raises(ValueError):
         tracing.decode(np.zeros((4, 9), np.uint64))
+
+
+def test_summarize_batched_by_size_class():
+    """Graph ids in bits 40-63 of word 0; tasks grouped by the size class of
+    their graph: graph 0 (n = 100, class n <= 128) has the pivot, graph 1
+    (n = 700, class n <= 1024) the two remaining tiles."""
+    t = _trace()
+    t[1, 0] |= np.uint64(1) << np.uint64(40)
+    t[2, 0] |= np.uint64(1) << np.uint64(40)
+    d = tracing.decode(t)
+    assert d["graph"].tolist() == [0, 1, 1] and d["type"].tolist() == [0, 3, 3]
+    s = tracing.summarize_batched(t, ns=[100, 700], bs_per_graph=[32, 64])
+    assert set(s["by_class"]) == {"n<=128", "n<=1024"}
+    small, mid = s["by_class"]["n<=128"], s["by_class"]["n<=1024"]
+    assert small["graphs"] == 1 and small["bs"] == [32] and small["pivot"]["tasks"] == 1
+    assert small["pivot"]["compute_us"] == pytest.approx(10.0)
+    assert small["pivot"]["input_wait_us"] == pytest.approx(2.0)
+    assert mid["remaining"]["tasks"] == 2 and mid["remaining"]["compute_us"] == pytest.approx(4.5)
+    # compute shares: pivot 10 us, tiles 5 + 4 us of 19 us
+    assert small["compute_share"] == pytest.approx(10 / 19)
+    assert s["compute_share_by_type"]["remaining"] == pytest.approx(9 / 19)
+    assert mid["span_us"] == pytest.approx((12500 - 1000) / 1e3)
+
+
+def test_critical_path_segments():
+    """A two-round chain built by hand: pivot(0) -> panels (0,1), (1,0) ->
+    remaining tile (1,1) of round 0 -> pivot(1); the segments are the gaps
+    between the chain's timestamps."""
+    # queue rows (type, round, ti, tj) of R = 2: task ids 0..7
+    q = [(0, 0, 0, 0), (1, 0, 0, 1), (2, 0, 1, 0), (3, 0, 1, 1), (0, 1, 1, 1),
+         (1, 1, 1, 0), (2, 1, 0, 1), (3, 1, 0, 0)]
+    rows = [
+        _row(0, 0, 0, 0, 0, 0, 1000, 3000, 3500),      # pivot: compute 2 us, publish 0.5
+        _row(1, 1, 1, 0, 0, 0, 4000, 6000, 6200),      # row panel
+        _row(2, 2, 2, 0, 0, 0, 4500, 7000, 7400),      # column panel (the later one)
+        _row(3, 3, 3, 0, 0, 0, 8000, 9000, 9100),      # remaining tile (1,1)
+        _row(4, 0, 4, 0, 0, 0, 10000, 12000, 12500),   # pivot(1)
+    ]
+    t = np.zeros((8, 10), np.uint64)
+    t[:5] = np.array(rows, dtype=np.uint64)
+    t[:5, 2] = 1   # claimed (non-zero rows are decoded)
+    cp = tracing.critical_path(t, q)
+    assert cp["rounds"] == 1
+    s = cp["segments_us"]
+    assert s["pivot"] == pytest.approx(2.0) and s["pivot_pub"] == pytest.approx(0.5)
+    assert s["to_panels"] == pytest.approx(1.0)      # 3.5 -> 4.5 (the later start)
+    assert s["panels"] == pytest.approx(2.5)         # 4.5 -> 7.0
+    assert s["panel_pub"] == pytest.approx(0.4)
+    assert s["to_tile"] == pytest.approx(0.6) and s["tile"] == pytest.approx(1.0)
+    assert s["tile_pub"] == pytest.approx(0.1) and s["to_pivot"] == pytest.approx(0.9)
+    assert cp["round_us"] == pytest.approx(9.0)      # 1.0 -> 10.0
