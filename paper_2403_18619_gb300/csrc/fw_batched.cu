@@ -4,10 +4,12 @@
 // Every graph keeps its own blocked-FW task queue (decode_task with its own R,
 // block size and lookahead) and its own flags and snapshots.  The plan
 // interleaves the graphs' queues into one global list in "stage waves": stage
-// 0 of every graph, then stage 1 of every graph, ... (largest graphs first).
-// Each graph's tasks keep their relative order, so the global list is still a
-// topological order of every graph's dependencies, and a small graph's
-// latency-bound pivot chain hides behind other graphs' min-plus work.  One
+// 0 of every graph, then stage 1 of every graph, ... (largest graphs first),
+// each wave phase by phase (every graph's pivots, then remaining tiles, then
+// panels, ...).  Each graph's tasks keep their relative order, so the global
+// list is still a topological order of every graph's dependencies, and a
+// graph's latency-bound pivot -> panel chain hides behind the other graphs'
+// min-plus work.  One
 // kernel (the warp-specialised engine with a runtime block size per task)
 // drains the list.
 //
@@ -210,12 +212,32 @@ fw_status plan_build(fw_batched_plan* p) {
   if (total >= (int64_t)1 << 31) return FW_ERR_UNSUPPORTED;
   std::vector<uint2> list;
   list.reserve(total);
+  // Stage waves, phase by phase: a graph's stage s is [pivot(s)] [its first
+  // remaining tiles of round s-1] [panels(s)] [the rest of round s-1]
+  // [round s's tiles in tile row / column s+1] (decode_task's layout), and the
+  // wave emits segment 0 of every graph, then segment 1 of every graph, ...
+  // So the tiles between one graph's pivot and its panels are every graph's
+  // (a pivot takes about as long as 3 remaining tiles, far more than its own
+  // graph's tiles cover when many graphs share the GPU), and each graph's own
+  // tasks keep their order: the list stays a topological order of every
+  // graph's dependencies.
   for (int s = 0; s <= maxR; ++s)
-    for (int64_t oi = 0; oi < B; ++oi) {
-      const int64_t g = order[oi];
-      if (s > p->R[g]) continue;
-      for (unsigned t = offs[g][s]; t < offs[g][s + 1]; ++t) list.push_back(make_uint2((unsigned)g, t));
-    }
+    for (int seg = 0; seg < 5; ++seg)
+      for (int64_t oi = 0; oi < B; ++oi) {
+        const int64_t g = order[oi];
+        const int R = p->R[g];
+        if (s > R) continue;
+        const int64_t np = s < R ? 2 * (int64_t)(R - 1) : 0;
+        const int64_t nrest = s >= 1 ? size_rest(R, s - 1) : 0;
+        const int64_t gl = s >= 1 && s < R ? std::min<int64_t>(look[g], nrest) : (s == R ? nrest : 0);
+        const int64_t len[5] = {s < R ? 1 : 0, gl, np, s >= 1 && s < R ? nrest - gl : 0,
+                                s < R ? size_L(R, s) : 0};
+        int64_t first = offs[g][s];
+        for (int k = 0; k < seg; ++k) first += len[k];
+        for (int64_t t = first; t < first + len[seg]; ++t)
+          list.push_back(make_uint2((unsigned)g, (unsigned)t));
+      }
+  if ((int64_t)list.size() != total) return FW_ERR_CUDA;  // the segments cover every stage
   p->ntasks = (int64_t)list.size();
   const size_t list_off = off;
   off += al(list.size() * sizeof(uint2));
