@@ -657,10 +657,10 @@ def main():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched and backward measurements")
     ap.add_argument("--config", default=None,
-                    help="time only this one of the other single-graph workloads "
-                         "(n1024_i32_bs32, n8192_i32_p0.5, n8192_f32_p0.5, "
-                         "n8192_f32_p0.5_distance_only, n8192_f64_p0.5, n8192_i64_p0.5) and "
-                         "print its result, e.g. to profile it")
+                    help="time only this one of the other workloads (n1024_i32_bs32, "
+                         "n8192_i32_p0.5, n8192_f32_p0.5, n8192_f32_p0.5_distance_only, "
+                         "n8192_f64_p0.5, n8192_i64_p0.5, backward, batched) and print its "
+                         "result, e.g. to profile it")
     ap.add_argument("--trace-config", nargs=2, default=None, metavar=("NAME", "OUT.json"),
                     help="trace one solve of a single-graph workload (as --config) and write "
                          "the trace summary and its per-round critical path")
@@ -686,6 +686,10 @@ def main():
         import torch
         import paper_2403_18619_gb300 as fw
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        if args.config in ("backward", "batched"):
+            fn = bench_backward if args.config == "backward" else bench_batched
+            print(json.dumps({"config": args.config, **fn(fw, args)}), flush=True)
+            return 0
         res = bench_configs(fw, args, only=args.config)
         if not res:
             raise SystemExit("unknown --config %r" % args.config)
