@@ -40,8 +40,13 @@ BS = 128
 SAMPLE_N = 2048          # CPU baseline: leading 2048-vertex induced subgraph
 # DRAM bytes (read + write) of one k_persistent_ws launch of the current
 # kernel, keyed by (n, BS, driver); null in the line where no capture exists.
-# Algorithmic: 8 n^3 / BS = 2.20e12 B at n = 32768, BS = 128.
-TRAFFIC_BYTES = {}
+# n = 32768: one ncu capture of the same kernel at n = 16384 (342.2e9 B)
+# scaled by n^3; an upper bound, since the bytes above the algorithmic
+# 8 n^3 / BS (2.20e12 B here) are scattered predecessor stores whose share
+# falls as n grows (1.31x at n = 8192, 1.24x at n = 16384).
+TRAFFIC_BYTES = {(32768, 128, 1): 342.2e9 * 8}
+TRAFFIC_NOTE = {(32768, 128, 1): "ncu dram bytes of one launch at n = 16384, scaled by n^3 "
+                                 "(upper bound; algorithmic 8 n^3 / BS = 2.20e12 B)"}
 
 
 def workload_name(n=N_FULL):
@@ -620,6 +625,7 @@ def run_gpu(args):
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": rps / 1e12,
                      "unit": "Trelax/s", "frac": achieved / rps,
                      "traffic": TRAFFIC_BYTES.get((n, args.bs, args.driver)),
+                     "traffic_source": TRAFFIC_NOTE.get((n, args.bs, args.driver)),
                      "kernel": "k_persistent_ws<int,128>",
                      "peak_source": "fw_peak_probe (__viaddmin_u32 chains on all SMs, same "
                                     "process, %.1f relax/SM-clk at %.0f MHz)" % (per_clk,
