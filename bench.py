@@ -598,7 +598,8 @@ def run_gpu(args):
         te = reduce_max(sum(times) / len(times), world)
         e2e = {"value": whole_job_rate(relax, world, te), "unit": "relax/s",
                "h2d_bytes_per_step": n * ld * 4, "d2h_bytes_per_step": 2 * n * ld * 4,
-               "ms_per_step": te * 1e3, "api": "fw_solve_host (pinned host buffers)"}
+               "ms_per_step": te * 1e3, "ms_each": [t * 1e3 for t in times],
+               "api": "fw_solve_host (pinned host buffers)"}
 
     if rank != 0:
         return 0
