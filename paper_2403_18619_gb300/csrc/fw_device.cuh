@@ -740,96 +740,60 @@ __device__ __forceinline__ void pivot_packed(const Args<T>& a, int r, void* smem
       }
   }
   stamp(1);
-  if constexpr (BS == 32) {
-    // One warp closes a 32 x 32 tile: lane j holds column j (32 keys), step
-    // kk takes row kk's key from its own register and column kk's keys from
-    // lane kk by shuffles -- no barrier per step, where the 256-thread loop
-    // below needs one (a BS = 32 solve's pivots sit on its critical path).
-    // The keys pass through shared memory (the region nxt takes later).
-    uint32_t* kt = reinterpret_cast<uint32_t*>(nxt);  // [BS][BS]
+  // broadcast of step 0: row 0 and column 0 (owner thread row / column 0, register 0)
+  if (ty == 0) {
 #pragma unroll
-    for (int mm = 0; mm < TM; ++mm)
+    for (int gg = 0; gg < NG; ++gg) {
+      uint32_t v[G];
 #pragma unroll
-      for (int nn = 0; nn < TM; ++nn) kt[Gm::idx(ty, mm) * BS + Gm::idx(tx, nn)] = acc[mm][nn];
-    bar_compute();
-    if (tid < 32) {
-      uint32_t k[BS];
-#pragma unroll
-      for (int i = 0; i < BS; ++i) k[i] = kt[i * BS + tid];
-#pragma unroll
-      for (int kk = 0; kk < BS; ++kk) {
-        const uint32_t rk = k[kk] & ~K::MASK;  // row kk of this column, code 0
-#pragma unroll
-        for (int i = 0; i < BS; ++i) {
-          // column kk with code kk + 1 (row and column kk do not change at step kk)
-          const uint32_t cv = (__shfl_sync(0xffffffffu, k[i], kk) & ~K::MASK) | (uint32_t)(kk + 1);
-          k[i] = __viaddmin_u32(cv, rk, k[i]);
-        }
-      }
-#pragma unroll
-      for (int i = 0; i < BS; ++i) kt[i * BS + tid] = k[i];
+      for (int q = 0; q < G; ++q) v[q] = acc[0][gg * G + q];
+      vstore<G>(rowK + gg * Gm::SPAN + tx * G, v);
     }
-    bar_compute();
-#pragma unroll
-    for (int mm = 0; mm < TM; ++mm)
-#pragma unroll
-      for (int nn = 0; nn < TM; ++nn) acc[mm][nn] = kt[Gm::idx(ty, mm) * BS + Gm::idx(tx, nn)];
-  } else {
-    // broadcast of step 0: row 0 and column 0 (owner thread row / column 0, register 0)
-    if (ty == 0) {
-#pragma unroll
-      for (int gg = 0; gg < NG; ++gg) {
-        uint32_t v[G];
-#pragma unroll
-        for (int q = 0; q < G; ++q) v[q] = acc[0][gg * G + q];
-        vstore<G>(rowK + gg * Gm::SPAN + tx * G, v);
-      }
-    }
-    if (tx == 0) {
-#pragma unroll
-      for (int gg = 0; gg < NG; ++gg) {
-        uint32_t v[G];
-#pragma unroll
-        for (int q = 0; q < G; ++q) v[q] = acc[gg * G + q][0] + 1u;
-        vstore<G>(colK + gg * Gm::SPAN + ty * G, v);
-      }
-    }
-    static_for<NG>([&](auto gc) {
-      constexpr int g = decltype(gc)::value;
-#pragma unroll 1
-      for (int to = 0; to < 16; ++to) {
-        static_for<G>([&](auto ec) {
-          constexpr int e = decltype(ec)::value;
-          const int kk = g * Gm::SPAN + to * G + e;  // row kk = register g*G+e of thread row to
-          const int buf = kk & 1;
-          bar_compute();
-          uint32_t cv[TM], rv[TM];
-#pragma unroll
-          for (int gg = 0; gg < NG; ++gg) {
-            uint32_t tc[G], tr[G];
-            vload_s<G>(tc, colK + buf * BS + gg * Gm::SPAN + ty * G);
-            vload_s<G>(tr, rowK + buf * BS + gg * Gm::SPAN + tx * G);
-#pragma unroll
-            for (int q = 0; q < G; ++q) { cv[gg * G + q] = tc[q]; rv[gg * G + q] = tr[q]; }
-          }
-          // row / column kk+1 first
-          if constexpr (e + 1 < G) {
-            pivot_publish_next<BS, g * G + e + 1>(acc, cv, rv, to, kk + 1, rowK, colK, tx, ty);
-          } else {
-            if (to < 15) {
-              pivot_publish_next<BS, g * G>(acc, cv, rv, to + 1, kk + 1, rowK, colK, tx, ty);
-            } else if constexpr (g + 1 < NG) {
-              pivot_publish_next<BS, (g + 1) * G>(acc, cv, rv, 0, kk + 1, rowK, colK, tx, ty);
-            }
-          }
-#pragma unroll
-          for (int mm = 0; mm < TM; ++mm)
-#pragma unroll
-            for (int nn = 0; nn < TM; ++nn) acc[mm][nn] = __viaddmin_u32(cv[mm], rv[nn], acc[mm][nn]);
-        });
-      }
-    });
   }
+  if (tx == 0) {
+#pragma unroll
+    for (int gg = 0; gg < NG; ++gg) {
+      uint32_t v[G];
+#pragma unroll
+      for (int q = 0; q < G; ++q) v[q] = acc[gg * G + q][0] + 1u;
+      vstore<G>(colK + gg * Gm::SPAN + ty * G, v);
+    }
+  }
+  static_for<NG>([&](auto gc) {
+    constexpr int g = decltype(gc)::value;
+#pragma unroll 1
+    for (int to = 0; to < 16; ++to) {
+      static_for<G>([&](auto ec) {
+        constexpr int e = decltype(ec)::value;
+        const int kk = g * Gm::SPAN + to * G + e;  // row kk = register g*G+e of thread row to
+        const int buf = kk & 1;
+        bar_compute();
+        uint32_t cv[TM], rv[TM];
+#pragma unroll
+        for (int gg = 0; gg < NG; ++gg) {
+          uint32_t tc[G], tr[G];
+          vload_s<G>(tc, colK + buf * BS + gg * Gm::SPAN + ty * G);
+          vload_s<G>(tr, rowK + buf * BS + gg * Gm::SPAN + tx * G);
+#pragma unroll
+          for (int q = 0; q < G; ++q) { cv[gg * G + q] = tc[q]; rv[gg * G + q] = tr[q]; }
+        }
+        // row / column kk+1 first
+        if constexpr (e + 1 < G) {
+          pivot_publish_next<BS, g * G + e + 1>(acc, cv, rv, to, kk + 1, rowK, colK, tx, ty);
+        } else {
+          if (to < 15) {
+            pivot_publish_next<BS, g * G>(acc, cv, rv, to + 1, kk + 1, rowK, colK, tx, ty);
+          } else if constexpr (g + 1 < NG) {
+            pivot_publish_next<BS, (g + 1) * G>(acc, cv, rv, 0, kk + 1, rowK, colK, tx, ty);
+          }
+        }
+#pragma unroll
+        for (int mm = 0; mm < TM; ++mm)
+#pragma unroll
+          for (int nn = 0; nn < TM; ++nn) acc[mm][nn] = __viaddmin_u32(cv[mm], rv[nn], acc[mm][nn]);
+      });
+    }
+  });
   stamp(2);
   // Chains of last steps: element (a, b) last improved at step kk takes the
   // final last hop of (kk, b), whose own last improving step is earlier; walk
