@@ -587,7 +587,9 @@ __device__ __forceinline__ void core_generic(const T* __restrict__ As, const T* 
                                              int kk0 = 0) {
   using Gm = Geo<BS>;
   constexpr int G = Gm::G, TM = Gm::TM;
-#pragma unroll 1
+  // 2 steps (n = 8192 fp32 with predecessors 105.6 -> 102.8 ms, int64 252 -> 246 ms;
+  // 4 and 8 spill at the 168-register cap of the persistent kernel)
+#pragma unroll 2
   for (int kk = 0; kk < K; ++kk) {
     T a[TM], b[TM];
 #pragma unroll
@@ -617,7 +619,8 @@ __device__ __forceinline__ void core_min(const T* __restrict__ As, const T* __re
                                          T (&acc)[Geo<BS>::TM][Geo<BS>::TM], int tx, int ty) {
   using Gm = Geo<BS>;
   constexpr int G = Gm::G, TM = Gm::TM;
-#pragma unroll 2
+  // 8 steps (n = 8192 fp32 distance-only 43.8 -> 42.4 ms)
+#pragma unroll 8
   for (int kk = 0; kk < K; ++kk) {
     T a[TM], b[TM];
 #pragma unroll
