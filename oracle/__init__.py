@@ -17,6 +17,11 @@ What each function is pinned to (tests/test_oracle.py):
   certificate_i64          hand-built correct/incorrect inputs (planted faults).
   path_count_i64           brute-force enumeration of shortest paths.
   grad_f64                 central finite differences of the fp64 oracle.
+  fw_k_i64 / fw_k_f64      brute-force enumeration of shortest simple paths
+                           (smallest largest-intermediate over them), closed
+                           forms (paths numbered up and down).
+  max_intermediate         brute-force enumeration on unique-path graphs, and
+                           fw_k_* on every pair with a unique shortest path.
 """
 from __future__ import annotations
 
@@ -64,6 +69,9 @@ def _load():
             lib.oracle_lasthop_margin_f64.argtypes = [P, P, P, I, P, I, P, ctypes.c_int]
             lib.oracle_lasthop_margin_i64.argtypes = [P, P, P, I, I, P, I, P, ctypes.c_int]
             lib.oracle_hops.argtypes = [P, I, P, I, P, ctypes.c_int]
+            lib.oracle_fw_k_i64.argtypes = [P, I, I, P, P, ctypes.c_int]
+            lib.oracle_fw_k_f64.argtypes = [P, I, P, P, ctypes.c_int]
+            lib.oracle_max_intermediate.argtypes = [P, I, P, I, P, ctypes.c_int]
             lib.oracle_grad_f64.argtypes = [P, P, I, P]
             _lib = lib
     return _lib
@@ -110,6 +118,47 @@ def fw_f64(W: np.ndarray, threads: int | None = None):
     lib.oracle_fw_f64(wp, n, D.ctypes.data, P.ctypes.data,
                       threads_default() if threads is None else threads)
     return D, P
+
+
+def fw_k_i64(W: np.ndarray, inf: int | None = None, threads: int | None = None):
+    """Fig. 1 with its path bookkeeping P_ij <- k (strict "<"): returns (D
+    int64, K int32), K[i][j] = the smallest over shortest i -> j paths of the
+    largest intermediate vertex, -1 where no relaxation improved (i, j)."""
+    lib = _load()
+    n = W.shape[0]
+    if inf is None:
+        inf = INF_I64 if np.asarray(W).dtype == np.int64 else INF_I32
+    W, wp = _c(W, np.int64)
+    D = np.empty((n, n), np.int64)
+    K = np.empty((n, n), np.int32)
+    lib.oracle_fw_k_i64(wp, n, inf, D.ctypes.data, K.ctypes.data,
+                        threads_default() if threads is None else threads)
+    return D, K
+
+
+def fw_k_f64(W: np.ndarray, threads: int | None = None):
+    """fw_k_i64 for real weights, in fp64: returns (D float64, K int32)."""
+    lib = _load()
+    n = W.shape[0]
+    W, wp = _c(W, np.float64)
+    D = np.empty((n, n), np.float64)
+    K = np.empty((n, n), np.int32)
+    lib.oracle_fw_k_f64(wp, n, D.ctypes.data, K.ctypes.data,
+                        threads_default() if threads is None else threads)
+    return D, K
+
+
+def max_intermediate(Prows, rows=None, threads=None):
+    """Largest intermediate vertex on each path a last-hop matrix records (-1:
+    diagonal, single edge, unreachable, or P not leading back to the source)."""
+    lib = _load()
+    P, pp = _c(Prows, np.int32)
+    n = P.shape[1]
+    r, rp, m = _rows(rows, n)
+    out = np.empty((m, n), np.int32)
+    lib.oracle_max_intermediate(pp, n, rp, m, out.ctypes.data,
+                                threads_default() if threads is None else threads)
+    return out
 
 
 def dijkstra_i64(W, sources, inf: int = INF_I32, threads: int | None = None):

@@ -95,6 +95,62 @@ void oracle_fw_f64(const double* W, i64 n, double* D, int32_t* P, int threads) {
   }
 }
 
+/* Fig. 1 (Sec. 2.3) as printed in its path bookkeeping: P[i][j] receives the
+   intermediate vertex k of the relaxation that last improved (i, j), -1 when
+   none did (the diagonal, a shortest path that is the edge itself, an
+   unreachable pair).  The comparison is the strict "<" of the functions above
+   (with ">=" the relaxations through k = i and k = j, which add D[i][i] = 0 or
+   D[j][j] = 0, would always tie and overwrite P).  The last improvement
+   happens at the first k for which a shortest path with every intermediate
+   vertex <= k exists, so K[i][j] is the smallest, over the shortest i -> j
+   paths, of the largest intermediate vertex on the path: on a unique shortest
+   path, its largest intermediate vertex.  D receives the distances. */
+void oracle_fw_k_i64(const i64* W, i64 n, i64 inf, i64* D, int32_t* K, int threads) {
+  OMP_THREADS(threads);
+  for (i64 i = 0; i < n * n; ++i) {
+    D[i] = W[i];
+    K[i] = -1;
+  }
+  for (i64 k = 0; k < n; ++k) {
+#pragma omp parallel for schedule(static)
+    for (i64 i = 0; i < n; ++i) {
+      i64 dik = D[i * n + k];
+      if (dik >= inf) continue;
+      for (i64 j = 0; j < n; ++j) {
+        i64 dkj = D[k * n + j];
+        if (dkj >= inf) continue;
+        if (dik + dkj < D[i * n + j]) {
+          D[i * n + j] = dik + dkj;
+          K[i * n + j] = (int32_t)k;
+        }
+      }
+    }
+  }
+}
+
+void oracle_fw_k_f64(const double* W, i64 n, double* D, int32_t* K, int threads) {
+  OMP_THREADS(threads);
+  for (i64 i = 0; i < n * n; ++i) {
+    D[i] = W[i];
+    K[i] = -1;
+  }
+  for (i64 k = 0; k < n; ++k) {
+#pragma omp parallel for schedule(static)
+    for (i64 i = 0; i < n; ++i) {
+      double dik = D[i * n + k];
+      if (isinf(dik)) continue;
+      for (i64 j = 0; j < n; ++j) {
+        double dkj = D[k * n + j];
+        if (isinf(dkj)) continue;
+        if (dik + dkj < D[i * n + j]) {
+          D[i * n + j] = dik + dkj;
+          K[i * n + j] = (int32_t)k;
+        }
+      }
+    }
+  }
+}
+
 /* ---------------------------------------------------------- Dijkstra ---- */
 
 /* Dense Dijkstra from each source in src[0..nsrc): textbook O(n^2) version.
@@ -320,6 +376,33 @@ void oracle_hops(const int32_t* Prows, i64 n, const i64* rows, i64 nrows, int32_
       i64 x = v, h = 0;
       while (x != s && x >= 0 && h <= n) { x = p[x]; h++; }
       hops[r * n + v] = (x == s) ? (int32_t)h : -1;
+    }
+  }
+}
+
+/* Largest intermediate vertex on the path that a last-hop matrix records:
+   walk from v back to the source s (row r of P belongs to source rows[r]) and
+   take the largest vertex met strictly between them.  -1 on the diagonal, for
+   a path that is a single edge, an unreachable v (P = -1) and a P that does
+   not lead back to s within n steps. */
+void oracle_max_intermediate(const int32_t* Prows, i64 n, const i64* rows, i64 nrows,
+                             int32_t* out, int threads) {
+  OMP_THREADS(threads);
+#pragma omp parallel for schedule(dynamic, 1)
+  for (i64 r = 0; r < nrows; ++r) {
+    i64 s = rows ? rows[r] : r;
+    const int32_t* p = Prows + r * n;
+    for (i64 v = 0; v < n; ++v) {
+      i64 best = -1, x = v, h = 0;
+      if (v != s) {
+        x = p[v];
+        while (x != s && x >= 0 && x < n && h <= n) {
+          if (x > best) best = x;
+          x = p[x];
+          h++;
+        }
+      }
+      out[r * n + v] = (x == s) ? (int32_t)best : -1;
     }
   }
 }

@@ -447,3 +447,127 @@ def test_grad_vs_finite_differences():
     assert checked_nonzero > 0
     # non-edges and the diagonal carry no gradient
     assert (GW[~np.isfinite(W)] == 0).all() and (np.diag(GW) == 0).all()
+
+
+# ------------------------------------------- Fig. 1's P_ij <- k convention ---
+
+def brute_force_mids(W, inf):
+    """For every pair: the shortest distance and, over the shortest simple
+    paths, the largest intermediate vertex of each (-1 for a single edge)."""
+    n = W.shape[0]
+    best = np.full((n, n), np.inf)
+    mids_of = [[[] for _ in range(n)] for _ in range(n)]
+    for s in range(n):
+        best[s, s] = 0
+        others = [v for v in range(n) if v != s]
+        for L in range(1, n):
+            for mids in itertools.permutations(others, L - 1):
+                for t in others:
+                    if t in mids:
+                        continue
+                    path = (s,) + mids + (t,)
+                    ws = [W[a, b] for a, b in zip(path[:-1], path[1:])]
+                    if any((np.isinf(w) if W.dtype.kind == "f" else w >= inf) for w in ws):
+                        continue
+                    c = float(sum(float(w) for w in ws))
+                    top = max(mids) if mids else -1
+                    if c < best[s, t]:
+                        best[s, t] = c
+                        mids_of[s][t] = [top]
+                    elif c == best[s, t]:
+                        mids_of[s][t].append(top)
+    return best, mids_of
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+@pytest.mark.parametrize("n", [5, 7])
+def test_fw_k_brute_force(seed, n):
+    """K[i][j] = the smallest over the shortest i -> j paths of the largest
+    intermediate vertex; max_intermediate of the last-hop matrix is the largest
+    intermediate vertex of one shortest path (the one P records)."""
+    W = graphgen.dense_graph_i32(n, seed=seed, p=0.6, lo=1, hi=4)  # many ties
+    best, mids_of = brute_force_mids(W, INF)
+    Dk, K = oracle.fw_k_i64(W)
+    D, P = oracle.fw_i64(W)
+    np.testing.assert_array_equal(Dk, D)
+    M = oracle.max_intermediate(P)
+    ties = 0
+    for s in range(n):
+        for t in range(n):
+            if s == t or np.isinf(best[s, t]):
+                assert K[s, t] == -1 and M[s, t] == -1
+                continue
+            assert K[s, t] == min(mids_of[s][t]), (s, t, mids_of[s][t])
+            assert M[s, t] in mids_of[s][t]
+            if len(mids_of[s][t]) == 1:
+                assert M[s, t] == K[s, t]
+            ties += len(set(mids_of[s][t])) > 1
+    assert ties > 0 or n == 5
+
+
+@pytest.mark.parametrize("seed", [21, 22])
+def test_fw_k_brute_force_float(seed):
+    n = 7
+    W = graphgen.dense_graph_f32(n, seed=seed, p=0.7)
+    best, mids_of = brute_force_mids(W, None)
+    Dk, K = oracle.fw_k_f64(W)
+    D, P = oracle.fw_f64(W)
+    np.testing.assert_array_equal(Dk, D)
+    M = oracle.max_intermediate(P)
+    for s in range(n):
+        for t in range(n):
+            if s == t or np.isinf(best[s, t]):
+                assert K[s, t] == -1 and M[s, t] == -1
+            elif len(mids_of[s][t]) == 1:
+                assert K[s, t] == M[s, t] == mids_of[s][t][0]
+
+
+def test_fw_k_closed_forms():
+    """A path numbered upwards has its largest intermediate next to the
+    target, one numbered downwards next to the source; a complete graph of
+    unit weights has no intermediates at all."""
+    n = 9
+    Wu = np.full((n, n), INF, np.int32)
+    np.fill_diagonal(Wu, 0)
+    for k in range(n - 1):
+        Wu[k, k + 1] = 2 + k % 3
+    Wd = Wu.T.copy()                      # edges k + 1 -> k
+    _, Ku = oracle.fw_k_i64(Wu)
+    _, Kd = oracle.fw_k_i64(Wd)
+    Mu = oracle.max_intermediate(oracle.fw_i64(Wu)[1])
+    Md = oracle.max_intermediate(oracle.fw_i64(Wd)[1])
+    for i in range(n):
+        for j in range(n):
+            up = j - 1 if j >= i + 2 else -1
+            down = i - 1 if i >= j + 2 else -1
+            assert Ku[i, j] == Mu[i, j] == up, (i, j)
+            assert Kd[i, j] == Md[i, j] == down, (i, j)
+    W1 = np.ones((12, 12), np.float32)
+    np.fill_diagonal(W1, 0)
+    assert (oracle.fw_k_f64(W1)[1] == -1).all()
+    assert (oracle.max_intermediate(oracle.fw_f64(W1)[1]) == -1).all()
+
+
+def test_fw_k_matches_max_intermediate_on_unique_paths():
+    """Two independent routes to the same number on every pair with a unique
+    shortest path: the k of Fig. 1's last improvement, and the walk of the
+    last-hop path."""
+    for n, seed in ((64, 3), (150, 4)):
+        W = graphgen.dense_graph_i32(n, seed=seed, p=0.3, lo=1, hi=1000)
+        Dk, K = oracle.fw_k_i64(W)
+        D, P = oracle.fw_i64(W)
+        M = oracle.max_intermediate(P)
+        cnt = oracle.path_count_i64(W, D)
+        uniq = (cnt == 1) & ~np.eye(n, dtype=bool) & (D < INF)
+        assert uniq.sum() > n * n // 2
+        np.testing.assert_array_equal(K[uniq], M[uniq])
+        # elsewhere Fig. 1 keeps the smallest such vertex over the shortest paths
+        assert (K <= M).all()
+
+
+def test_max_intermediate_invalid_pred():
+    """A last-hop matrix that does not lead back to the source yields -1."""
+    P = np.array([[-1, 2, 1], [1, -1, 1], [2, 2, -1]], np.int32)  # 0: 1 <-> 2 cycle
+    M = oracle.max_intermediate(P)
+    assert M[0, 1] == -1 and M[0, 2] == -1
+    assert M[1, 0] == -1 and M[1, 2] == -1 and M[2, 0] == -1 and M[2, 1] == -1
