@@ -412,6 +412,43 @@ def bench_backward(fw, args):
             "speedup_vs_one_launch_per_graph": t_single / (fwd + bwd)}
 
 
+# Algorithmic bytes per entry of fw_intermediate: read pred, write the result.
+MID_BYTES_PER_ENTRY = 8
+
+
+def bench_intermediate(fw, args):
+    """fw_intermediate (the paper's P_ij = k bookkeeping from last hops) on the
+    predecessors of an 8192-vertex int32 solve (p = 0.5, weights U[1, 100])."""
+    import torch
+    import graphgen.device as gdev
+    n = 8192
+    D = torch.empty((n, n), dtype=torch.int32, device="cuda")
+    P = torch.empty_like(D)
+    gdev.fill_i32(D, seed=8192, p=0.5, lo=1, hi=100)
+    fw.fw_solve(D, P)
+    out = torch.empty_like(P)
+    for _ in range(3):
+        fw.fw_intermediate(P, out=out)
+    fw.fw_sync_status()
+    steps = max(5, args.steps)
+    ev = _events(steps + 1)
+    ev[0].record()
+    for i in range(steps):
+        fw.fw_intermediate(P, out=out)   # 512 MB in, 256 MB written: larger than L2
+        ev[i + 1].record()
+    torch.cuda.synchronize()
+    ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(steps)]
+    avg = sum(ms) / steps
+    hbm, src = _peaks()
+    algo = float(n) * n * MID_BYTES_PER_ENTRY
+    return {"workload": "pred of an 8192-vertex int32 solve, p=0.5", "ms": avg,
+            "roofline": {"bound": "hbm", "algorithmic_bytes": algo,
+                         "bytes_per_entry": MID_BYTES_PER_ENTRY,
+                         "achieved_gbs": algo / (avg * 1e-3) / 1e9, "peak_gbs": hbm,
+                         "frac": algo / (avg * 1e-3) / 1e9 / hbm,
+                         "peak_source": "%s copy bandwidth" % src}}
+
+
 def _single_configs(fw):
     """(name, n, dtype, edge p, BS (0: automatic), generator arguments, seed,
     with predecessors) of the single-graph workloads besides the headline."""
@@ -641,6 +678,7 @@ def run_gpu(args):
     if not args.no_extras and world == 1:
         line["batched"] = bench_batched(fw, args)
         line["backward"] = bench_backward(fw, args)
+        line["intermediate"] = bench_intermediate(fw, args)
         line["configs"] = bench_configs(fw, args)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
@@ -666,7 +704,8 @@ def main():
     ap.add_argument("--config", default=None,
                     help="time only this one of the other workloads (n1024_i32_bs32, "
                          "n8192_i32_p0.5, n8192_f32_p0.5, n8192_f32_p0.5_distance_only, "
-                         "n8192_f64_p0.5, n8192_i64_p0.5, backward, batched) and print its "
+                         "n8192_f64_p0.5, n8192_i64_p0.5, backward, batched, intermediate) and "
+                         "print its "
                          "result, e.g. to profile it")
     ap.add_argument("--trace-config", nargs=2, default=None, metavar=("NAME", "OUT.json"),
                     help="trace one solve of a single-graph workload (as --config) and write "
@@ -693,8 +732,10 @@ def main():
         import torch
         import paper_2403_18619_gb300 as fw
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-        if args.config in ("backward", "batched"):
-            fn = bench_backward if args.config == "backward" else bench_batched
+        extra = {"backward": bench_backward, "batched": bench_batched,
+                 "intermediate": bench_intermediate}
+        if args.config in extra:
+            fn = extra[args.config]
             print(json.dumps({"config": args.config, **fn(fw, args)}), flush=True)
             return 0
         res = bench_configs(fw, args, only=args.config)

@@ -314,6 +314,28 @@ fw_status fw_paths(const int32_t* pred, int64_t n, int64_t ld, const int32_t* sr
                    int32_t* len, void* stream);
 
 /*
+ * fw_intermediate: the path matrix in the bookkeeping of the paper's Fig. 1
+ * (Sec. 2.3), where P_ij is the intermediate vertex k through which (i, j)
+ * last improved.  For every pair, out[i][j] = the largest vertex strictly
+ * between i and j on the path that the last-hop matrix pred records; -1 on
+ * the diagonal, for a path that is a single edge, for an unreachable pair
+ * (pred -1) and where pred does not lead back to the source.  On a pair with
+ * a unique shortest path this is exactly the k of Fig. 1's last improvement
+ * (strict "<"); with several shortest paths it is the largest intermediate
+ * of the recorded one, and a path rebuilds recursively from it: the paths
+ * i -> k and k -> j joined at k.
+ * pred: device, batch matrices of n x ld int32 (a solve's last hops), matrix
+ * b at pred + b * stride.  out: device, same layout; out == pred (in place)
+ * is allowed, a partial overlap is not.  Asynchronous on stream.  FW_ERR_ARG
+ * for null pointers, n < 1, ld < n, batch < 0, stride < n * ld when
+ * batch > 1, or batch * n >= 2^31; FW_ERR_UNSUPPORTED for n > 57344 (the
+ * kernel keeps 4 bytes per vertex of a row in shared memory); batch = 0 is a
+ * no-op.
+ */
+fw_status fw_intermediate(const int32_t* pred, int32_t* out, int64_t n, int64_t ld,
+                          int64_t batch, int64_t stride, void* stream);
+
+/*
  * fw_solve_plan: what fw_solve_ex would choose for n vertices and *opt (NULL:
  * defaults) on a GPU with `sms` co-resident CTAs (one per SM): the block size
  * BS, the number of rounds R = ceil(n / BS) (Sec. 2.3), the lookahead of the

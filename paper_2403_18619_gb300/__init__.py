@@ -18,7 +18,7 @@ __all__ = [
     "FWError", "Options", "load", "check", "fw_solve", "fw_solve_ex", "fw_solve_host",
     "fw_solve_noalloc", "fw_sync_status", "fw_backward", "fw_backward_strided",
     "fw_peak_probe", "fw_verify_certificate", "fw_release_workspace", "fw_solve_plan",
-    "fw_queue_tasks", "fw_paths", "fw_tile_closure", "fw_tile_minplus", "fw_block_init_pred",
+    "fw_queue_tasks", "fw_paths", "fw_intermediate", "fw_tile_closure", "fw_tile_minplus", "fw_block_init_pred",
     "BatchedPlan", "fw_bs_table", "fw_autotune_bs", "padded", "solve",
     "solve_batched", "INF_I32", "INF_I64", "FW_I32", "FW_F32", "FW_I64", "FW_F64", "DRIVER_AUTO",
     "DRIVER_PERSISTENT", "DRIVER_PHASED",
@@ -106,6 +106,7 @@ def load():
         lib.fw_queue_tasks.argtypes = [I32, I64, I64, I64, P]
         lib.fw_solve_plan.argtypes = [I64, P, I32, P, P, P, P]
         lib.fw_paths.argtypes = [P, I64, I64, P, P, I64, P, I64, P, P]
+        lib.fw_intermediate.argtypes = [P, P, I64, I64, I64, I64, P]
         lib.fw_solve_noalloc.argtypes = [P, P, I64, I64, I32, P]
         lib.fw_tile_closure.argtypes = [P, P, I64, I32, I32, P]
         lib.fw_tile_minplus.argtypes = [P, P, I64, P, I64, P, I64, P, I64, I64, I64, I32, I64,
@@ -119,7 +120,8 @@ def load():
                      "fw_backward", "fw_backward_strided", "fw_sync_status",
                      "fw_release_workspace", "fw_peak_probe", "fw_verify_certificate",
                      "fw_queue_tasks", "fw_solve_noalloc", "fw_bs_table", "fw_autotune_bs",
-                     "fw_solve_plan", "fw_paths", "fw_tile_closure", "fw_tile_minplus",
+                     "fw_solve_plan", "fw_paths", "fw_intermediate", "fw_tile_closure",
+                     "fw_tile_minplus",
                      "fw_block_init_pred"):
             getattr(lib, name).restype = I32
         _lib = lib
@@ -291,6 +293,31 @@ def fw_paths(pred, src, dst, max_len: int, stream=None):
     check(load().fw_paths(pp, n, ld, src.data_ptr(), dst.data_ptr(), m, out.data_ptr(),
                           int(max_len), lens.data_ptr(), _stream_ptr(stream)), "fw_paths")
     return out, lens
+
+
+def fw_intermediate(pred, out=None, stream=None):
+    """fw_intermediate on CUDA int32 tensors: pred an (n, n) or (B, n, n) view
+    of solved last hops (unit column stride).  Returns out (a new tensor of
+    pred's shape, or the given one; out=pred works in place): the largest
+    intermediate vertex of each recorded path, -1 where the path has none or
+    there is no path -- the k of the paper's Fig. 1 on unique shortest paths."""
+    import torch
+    if not isinstance(pred, torch.Tensor) or not pred.is_cuda or pred.dtype != torch.int32:
+        raise TypeError("pred must be an int32 CUDA tensor")
+    if pred.dim() not in (2, 3) or pred.shape[-1] != pred.shape[-2] or pred.stride(-1) != 1:
+        raise ValueError("pred must be an (n, n) or (B, n, n) view with unit column stride")
+    if out is None:
+        out = torch.empty_strided(pred.shape, pred.stride(), dtype=torch.int32,
+                                  device=pred.device)
+    if out.shape != pred.shape or out.stride() != pred.stride() or out.dtype != torch.int32 \
+            or out.device != pred.device:
+        raise ValueError("out must be an int32 tensor with pred's shape, strides and device")
+    n, ld = pred.shape[-1], pred.stride(-2)
+    B = pred.shape[0] if pred.dim() == 3 else 1
+    stride = pred.stride(0) if pred.dim() == 3 else n * ld
+    check(load().fw_intermediate(pred.data_ptr(), out.data_ptr(), n, ld, B, stride,
+                                 _stream_ptr(stream)), "fw_intermediate")
+    return out
 
 
 def fw_solve_plan(n: int, options: Options | None = None, sms: int = 152) -> dict:

@@ -185,6 +185,21 @@ def test_paths_argument_checks(fw):
     assert lib.fw_paths(p, 10, 10, p, p, 0, p, 4, p, None) == 0
 
 
+def test_intermediate_argument_checks(fw):
+    """fw_intermediate's host checks (no launch; batch 0 is a no-op)."""
+    lib = fw.load()
+    p = ctypes.c_void_p(16)
+    assert lib.fw_intermediate(None, p, 10, 10, 1, 100, None) == 1
+    assert lib.fw_intermediate(p, None, 10, 10, 1, 100, None) == 1
+    assert lib.fw_intermediate(p, p, 0, 10, 1, 100, None) == 1
+    assert lib.fw_intermediate(p, p, 10, 8, 1, 100, None) == 1
+    assert lib.fw_intermediate(p, p, 10, 12, -1, 120, None) == 1
+    assert lib.fw_intermediate(p, p, 10, 12, 2, 119, None) == 1     # stride < n * ld
+    assert lib.fw_intermediate(p, p, 57345, 57348, 1, 0, None) == 6
+    assert lib.fw_intermediate(p, p, 50000, 50000, 50000, 50000 * 50000, None) == 1
+    assert lib.fw_intermediate(p, p, 10, 12, 0, 0, None) == 0
+
+
 def test_wide_dtype_and_tile_call_host_checks(fw):
     """Checks made on the host before any CUDA call: 64-bit dtypes take BS 32
     or 64, and the tile-level calls reject bad block sizes, dtypes, leading
