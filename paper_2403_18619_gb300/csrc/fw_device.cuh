@@ -120,6 +120,15 @@ __device__ __forceinline__ void tma_store_2d(const void* tmap, int x, int y, con
 __device__ __forceinline__ void bulk_commit_wait_all() {
   asm volatile("cp.async.bulk.commit_group;\n cp.async.bulk.wait_group 0;" ::: "memory");
 }
+// Commit this thread's bulk stores and wait until their shared-memory source
+// has been read (the buffer may be reused; the writes may still be in flight).
+__device__ __forceinline__ void bulk_commit_wait_read() {
+  asm volatile("cp.async.bulk.commit_group;\n cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+// Wait until every bulk store this thread committed has been performed.
+__device__ __forceinline__ void bulk_wait_all() {
+  asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
 // Order this thread's earlier generic shared-memory accesses before its
 // following async-proxy (TMA) accesses.
 __device__ __forceinline__ void fence_proxy_async_shared() {
@@ -511,9 +520,13 @@ __device__ __forceinline__ int bound_of(T v) {
 // still records k: a later strict improvement of (k, j) through block r'
 // improves (i, j) through block r' as well (integer sums are exact).  So the
 // last hop of (i, j) is that of (k, j), which may itself be a via code of an
-// earlier round; pivot and panel tasks copy such entries as they are, and
-// k_resolve_pred follows each chain (at most R links, each to an earlier
-// round) once the solve is done.  fp32 keeps gathering real last hops: float
+// earlier round; pivot tasks copy such entries as they are, and
+// k_resolve_pred follows each chain once the solve is done.  The persistent
+// driver's panel tasks record via codes too: a row-panel entry (i, j) improved
+// through k of block r names (k, j) of the same tile, which that panel left
+// unchanged (had (k, j) improved through k', (i, j) would do better through
+// k', the pivot being closed); a column-panel entry names (k, j) of the
+// closed pivot.  fp32 keeps gathering real last hops: float
 // sums are not associative, and the argument needs them to be.
 template <typename T>
 struct ViaPred {
@@ -521,9 +534,14 @@ struct ViaPred {
 };
 __device__ __forceinline__ int32_t via_code(int64_t k) { return (int32_t)(-(k + 2)); }
 // The last hop that entry p of column j stands for (p itself unless a via code).
+// A chain takes at most two links per round (a remaining tile's code names an
+// entry of its row-panel tile, whose own code, if it has one from the same
+// round, names an entry that round left unchanged), so 2 * 1024 + 2 links
+// cover every solve; the cap only bounds the walk on a corrupted matrix.
 __device__ __forceinline__ int32_t resolve_pred(int32_t p, const int32_t* P, int64_t ld,
                                                 int64_t j) {
-  for (int hop = 0; p <= -2 && hop <= 1024; ++hop) p = P[(int64_t)(-(int64_t)p - 2) * ld + j];
+  for (int hop = 0; p <= -2 && hop <= 2 * 1024 + 2; ++hop)
+    p = P[(int64_t)(-(int64_t)p - 2) * ld + j];
   return p;
 }
 
@@ -1142,7 +1160,9 @@ __device__ __forceinline__ void stage_tile_i32(int32_t* dst, const int32_t* M, i
 // new values s and new predecessors np, with improved flags.  Stores them
 // (live tile, snapshot) and returns their bound.  Working one group at a time
 // keeps the epilogue's live registers at a quarter of a full micro-tile.
-template <typename T, int BS, bool is_row>
+// kSparseP: a row tile too stores the predecessors of its improved entries
+// only (the others keep theirs), as "via" codes do not need the full row.
+template <typename T, int BS, bool is_row, bool kSparseP = false>
 __device__ __forceinline__ int panel_store_group(const Args<T>& a, int r, int t, int g,
                                                  const T (&sv)[Geo<BS>::G][Geo<BS>::TM],
                                                  const int32_t (&np)[Geo<BS>::G][Geo<BS>::TM],
@@ -1175,19 +1195,27 @@ __device__ __forceinline__ int panel_store_group(const Args<T>& a, int r, int t,
           vstore<G>(a.D + gi * a.ld + gj0, vs);
           if (!a.P) {
             // distance-only
-          } else if constexpr (is_row) {
+          } else if constexpr (is_row && !kSparseP) {
             vstore<G>(a.P + gi * a.ld + gj0, vp);
           } else {
+            bool all = true;
 #pragma unroll
-            for (int q = 0; q < G; ++q)
-              if (imp[e][gg * G + q]) a.P[gi * a.ld + gj0 + q] = vp[q];
+            for (int q = 0; q < G; ++q) all &= imp[e][gg * G + q];
+            if (all) {
+              vstore<G>(a.P + gi * a.ld + gj0, vp);  // (early rounds: most groups)
+            } else {
+#pragma unroll
+              for (int q = 0; q < G; ++q)
+                if (imp[e][gg * G + q]) a.P[gi * a.ld + gj0 + q] = vp[q];
+            }
           }
         } else {
 #pragma unroll
           for (int q = 0; q < G; ++q)
             if (gj0 + q < a.n) {
               a.D[gi * a.ld + gj0 + q] = vs[q];
-              if (a.P && (is_row || imp[e][gg * G + q])) a.P[gi * a.ld + gj0 + q] = vp[q];
+              if (a.P && ((is_row && !kSparseP) || imp[e][gg * G + q]))
+                a.P[gi * a.ld + gj0 + q] = vp[q];
             }
         }
       }

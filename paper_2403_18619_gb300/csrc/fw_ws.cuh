@@ -77,7 +77,7 @@ struct WsBars {
   uint64_t chunk_full[2], chunk_empty[2];
   uint64_t d_full, d_empty, p_full, p_empty, task_done;
   uint64_t pub_full[kPubDepth], pub_empty[kPubDepth];
-  int desc[2][8];           // t, type, r, ti, tj, fast, graph
+  int desc[2][8];           // t, type, r, ti, tj, fast, graph, key operands
   int pubq[kPubDepth][6];   // t, type, r, ti, tj, graph of tasks awaiting publication
 };
 
@@ -129,6 +129,8 @@ struct TileCtx {
 // with a copy (0: none), and stops arming once a wait has given up: arming a
 // phase whose predecessor has not completed would add its bytes to the wrong
 // phase.
+// (The drain waits on the LAST phase of each barrier: a parity wait can only
+// tell the latest two phases apart.)
 struct PipeCnt {
   unsigned d = 0, chunk = 0, p = 0;
   unsigned d_armed = 0, p_armed = 0, chunk_armed[2] = {0, 0};
@@ -137,13 +139,51 @@ struct PipeCnt {
 
 // ------------------------------------------------------------ compute side ----
 
+// In-place decode of `count` packed keys (int32 path) back to values, for a
+// remaining tile relaxed with compare and select whose panel wrote its key
+// snapshot only (exact: every finite value was below CAP).  Compute warps
+// only; the caller synchronises them before reading the buffer.
+template <int BS>
+__device__ __forceinline__ void decode_keys(uint32_t* buf, int count) {
+  using K = Keys<BS>;
+  for (int i = (int)threadIdx.x * 4; i < count; i += kThreads * 4) {
+    uint4 v = *reinterpret_cast<uint4*>(buf + i);
+    auto d = [](uint32_t k) -> uint32_t {
+      const uint32_t x = k >> K::KB;
+      return x == (uint32_t)K::CAP ? (uint32_t)Num<int32_t>::inf() : x;
+    };
+    v.x = d(v.x);
+    v.y = d(v.y);
+    v.z = d(v.z);
+    v.w = d(v.w);
+    *reinterpret_cast<uint4*>(buf + i) = v;
+  }
+}
+
+// Operands of a compare-and-select remaining tile that arrive as keys: decode
+// them in the ring stage (bit 0: A, bit 1: B; every warp has waited for the
+// stage to fill, so no warp still reads its previous contents) and
+// synchronise the compute warps.
+template <typename T, int BS, int CK>
+__device__ __forceinline__ void decode_chunk(unsigned char* stage, int dec) {
+  if constexpr (Num<T>::kPacked) {
+    if (!dec) return;
+    uint32_t* As = reinterpret_cast<uint32_t*>(stage);
+    if (dec & 1) decode_keys<BS>(As, CK * BS);
+    if (dec & 2) decode_keys<BS>(As + CK * BS, CK * BS);
+    fence_proxy_async_shared();  // generic writes before the stage's next TMA fill
+    bar_compute();
+  }
+}
+
 // Distance-only remaining-tile task (no predecessors, generic kernel): add +
 // min over the streamed chunks, then the whole tile written back (unchanged
 // entries rewrite their own value).  A function of its own, so that the
 // packed kernel's register allocation does not see it.
 template <typename T, int BS, int LBS>
-__device__ __noinline__ bool ws_minplus_dist(TileCtx<T> c, int ti, int tj, unsigned char* smem,
-                                             WsBars* wb, PipeCnt& pc, uint64_t* tr) {
+__device__ __noinline__ bool ws_minplus_dist(TileCtx<T> c, int ti, int tj, int dec,
+                                             unsigned char* smem, WsBars* wb, PipeCnt& pc,
+                                             uint64_t* tr) {
   using Gm = Geo<BS>;
   using L = WsLayout<LBS, T>;
   using C = WsChunk<BS, T>;
@@ -183,6 +223,7 @@ __device__ __noinline__ bool ws_minplus_dist(TileCtx<T> c, int ti, int tj, unsig
                    c.timeout_ns))
       return false;
     if (tr) cw += clock64() - w0;
+    decode_chunk<T, BS, C::CK>(ring + st * L::kStage, dec);
     const T* As = reinterpret_cast<const T*>(ring + st * L::kStage);
     const T* Bs = As + C::CK * BS;
     core_min<BS, T, C::CK>(As, Bs, acc, tx, ty);
@@ -225,10 +266,10 @@ __device__ __noinline__ bool ws_minplus_dist(TileCtx<T> c, int ti, int tj, unsig
 // Remaining-tile task (phase 4 of round r, tile ti,tj).  Returns false if an
 // operand never arrived (the kernel then stops).
 template <typename T, int BS, int LBS>
-__device__ __forceinline__ bool ws_minplus(TileCtx<T> c, int ti, int tj, bool fast,
+__device__ __forceinline__ bool ws_minplus(TileCtx<T> c, int ti, int tj, bool fast, int dec,
                                         unsigned char* smem, WsBars* wb, PipeCnt& pc,
                                         uint64_t* tr) {
-  if (!fast && !c.P) return ws_minplus_dist<T, BS, LBS>(c, ti, tj, smem, wb, pc, tr);
+  if (!fast && !c.P) return ws_minplus_dist<T, BS, LBS>(c, ti, tj, dec, smem, wb, pc, tr);
   using Gm = Geo<BS>;
   using K = Keys<BS>;
   using L = WsLayout<LBS, T>;
@@ -370,6 +411,7 @@ __device__ __forceinline__ bool ws_minplus(TileCtx<T> c, int ti, int tj, bool fa
                      c.timeout_ns))
         return false;
       if (tr) cw += clock64() - w0;
+      decode_chunk<T, BS, C::CK>(ring + st * L::kStage, dec);
       const T* As = reinterpret_cast<const T*>(ring + st * L::kStage);
       const T* Bs = As + C::CK * BS;
       core_generic<BS, T, C::CK>(As, Bs, old, arg, tx, ty, ch * C::CK);
@@ -414,18 +456,316 @@ __device__ __forceinline__ bool ws_minplus(TileCtx<T> c, int ti, int tj, bool fa
   return true;
 }
 
+// Relaxation and epilogue of a producer-fed panel task (ws_panel) whose
+// operands are staged: packed keys (kFast) or raw values, A transposed in the
+// scratch stage, B in natural layout (Dbuf for a row tile, the pivot stage
+// for a column tile).  The accumulators start from the tile's own values as
+// staged there.  A function of its own per path, so that the two register
+// sets are never live together.
+template <typename T, int BS, int LBS, bool is_row, bool kFast>
+__device__ __noinline__ bool ws_panel_finish(const Args<T>& a, int r, int t, T* Dbuf, T* Piv,
+                                             unsigned char* scratch, WsBars* wb, CtaScratch* cs,
+                                             PipeCnt& pc) {
+  using Gm = Geo<BS>;
+  using K = Keys<BS>;
+  constexpr int TM = Gm::TM, G = Gm::G;
+  using U = std::conditional_t<kFast, uint32_t, T>;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4, lane = tid & 31;
+  const U* As = reinterpret_cast<const U*>(scratch);
+  const U* Bs = reinterpret_cast<const U*>(is_row ? Dbuf : Piv);
+  U acc[TM][TM];
+  if constexpr (is_row) {
+    // own values: B-form in Dbuf
+#pragma unroll
+    for (int m = 0; m < TM; ++m)
+#pragma unroll
+      for (int g = 0; g < Gm::NG; ++g) {
+        U v[G];
+        vload_s<G>(v, Bs + Gm::idx(ty, m) * BS + g * Gm::SPAN + tx * G);
+#pragma unroll
+        for (int e = 0; e < G; ++e) acc[m][g * G + e] = v[e];
+      }
+  } else {
+    // own values: A-form in the scratch stage (keys with their column's code)
+#pragma unroll
+    for (int nn = 0; nn < TM; ++nn)
+#pragma unroll
+      for (int g = 0; g < Gm::NG; ++g) {
+        U v[G];
+        vload_s<G>(v, As + Gm::idx(tx, nn) * BS + g * Gm::SPAN + ty * G);
+#pragma unroll
+        for (int e = 0; e < G; ++e) {
+          if constexpr (kFast) acc[g * G + e][nn] = v[e] & ~K::MASK;
+          else acc[g * G + e][nn] = v[e];
+        }
+      }
+  }
+  int code[kFast ? 1 : TM][kFast ? 1 : TM];
+  if constexpr (kFast) {
+    core_packed<BS>(As, Bs, acc, tx, ty);
+  } else {
+#pragma unroll
+    for (int m = 0; m < TM; ++m)
+#pragma unroll
+      for (int nn = 0; nn < TM; ++nn) code[m][nn] = 0;
+    core_generic<BS, T>(As, Bs, acc, code, tx, ty);
+  }
+  // operands consumed: order this warp's shared-memory writes before the
+  // copies that will overwrite the buffers, then release them
+  fence_proxy_async_shared();
+  __syncwarp();
+  if (lane == 0) {
+    const unsigned s0 = pc.chunk & 1;
+    mbar_arrive(&wb->d_empty);
+    mbar_arrive(&wb->chunk_empty[s0]);
+    mbar_arrive(&wb->chunk_empty[s0 ^ 1]);
+  }
+  ++pc.d;
+  pc.chunk += 2;
+  stamp(2);
+
+  // new values: their bound (the remaining tiles' packed-key test)
+  auto value = [&](int m, int nn) -> T {
+    if constexpr (kFast) {
+      const int32_t v = (int32_t)(acc[m][nn] >> K::KB);
+      return v == K::CAP ? Num<T>::inf() : (T)v;
+    } else {
+      return acc[m][nn];
+    }
+  };
+  auto codeof = [&](int m, int nn) -> int {
+    if constexpr (kFast) return (int)(acc[m][nn] & K::MASK);
+    else return code[m][nn];
+  };
+  // (fast path: the accumulator without its code is the value's key)
+  auto key = [&](int m, int nn) -> uint32_t {
+    if constexpr (kFast) return acc[m][nn] & ~K::MASK;
+    else return key_of<BS>((int32_t)acc[m][nn]);
+  };
+  int nb = 0;
+#pragma unroll
+  for (int m = 0; m < TM; ++m)
+#pragma unroll
+    for (int nn = 0; nn < TM; ++nn) nb = max(nb, bound_of<BS>(value(m, nn)));
+  int dummy = 0;
+  block_max2(nb, dummy, cs);
+  // keys are exact while every finite value is below CAP; otherwise (or
+  // without packed keys) the raw snapshot is written as well
+  const bool keys = a.packed != 0;
+  const bool raw = !keys || nb >= K::CAP;
+  const int slot = r & 1;
+  const size_t tile_off = ((size_t)slot * a.slot_tiles + t) * BS * BS;
+
+  // the live tile (values, and via codes k = r*BS + code - 1 where improved);
+  // a row tile's snapshots in the same (B-form) order
+  const int32_t via0 = via_code((int64_t)r * BS - 1);
+  const int ti = is_row ? r : t, tj = is_row ? t : r;
+#pragma unroll
+  for (int m = 0; m < TM; ++m) {
+    const int lr = Gm::idx(ty, m);
+    const int64_t gi = (int64_t)ti * BS + lr;
+#pragma unroll
+    for (int gg = 0; gg < Gm::NG; ++gg) {
+      const int lc0 = gg * Gm::SPAN + tx * G;
+      const int64_t gj0 = (int64_t)tj * BS + lc0;
+      T vs[G];
+      int32_t vp[G];
+      bool all = true;
+      int cq[G];
+#pragma unroll
+      for (int q = 0; q < G; ++q) {
+        vs[q] = value(m, gg * G + q);
+        cq[q] = codeof(m, gg * G + q);
+        vp[q] = via0 - cq[q];
+        all &= cq[q] != 0;
+      }
+      if (gi < a.n) {
+        if (gj0 + G <= a.n) {
+          vstore<G>(a.D + gi * a.ld + gj0, vs);
+          if (a.P) {
+            if (all) {
+              vstore<G>(a.P + gi * a.ld + gj0, vp);  // (early rounds: most groups)
+            } else {
+#pragma unroll
+              for (int q = 0; q < G; ++q)
+                if (cq[q]) a.P[gi * a.ld + gj0 + q] = vp[q];
+            }
+          }
+        } else {
+#pragma unroll
+          for (int q = 0; q < G; ++q)
+            if (gj0 + q < a.n) {
+              a.D[gi * a.ld + gj0 + q] = vs[q];
+              if (a.P && cq[q]) a.P[gi * a.ld + gj0 + q] = vp[q];
+            }
+        }
+      }
+      if constexpr (is_row) {
+        if (keys) {
+          uint32_t kq[G];
+#pragma unroll
+          for (int q = 0; q < G; ++q) kq[q] = key(m, gg * G + q);
+          vstore<G>(a.rowK + tile_off + lr * BS + lc0, kq);
+        }
+        if (raw) vstore<G>(a.rowR + tile_off + lr * BS + lc0, vs);
+      }
+    }
+  }
+  if constexpr (!is_row) {
+    // a column tile's snapshots: A-form (transposed), keys with code = column + 1
+#pragma unroll
+    for (int nn = 0; nn < TM; ++nn) {
+      const int lc = Gm::idx(tx, nn);
+#pragma unroll
+      for (int g = 0; g < Gm::NG; ++g) {
+        const size_t off = tile_off + (size_t)lc * BS + g * Gm::SPAN + ty * G;
+        if (keys) {
+          uint32_t kq[G];
+#pragma unroll
+          for (int e = 0; e < G; ++e) kq[e] = key(g * G + e, nn) + (uint32_t)lc + 1u;
+          vstore<G>(a.colK + off, kq);
+        }
+        if (raw) {
+          T vs[G];
+#pragma unroll
+          for (int e = 0; e < G; ++e) vs[e] = value(g * G + e, nn);
+          vstore<G>(a.colR + off, vs);
+        }
+      }
+    }
+  }
+  if (tid == 0) {
+    int32_t* bnd = is_row ? a.rowB : a.colB;
+    bnd[(size_t)slot * a.slot_tiles + t] = nb;
+  }
+  stamp(3);
+  return true;
+}
+
+// Panel task of round r (int32), fed by the producer like a remaining tile:
+// Dbuf holds the tile's own values, ring stage s0 the closed pivot (snapshot
+// of slot r&1, natural layout) and stage s1 is scratch for the transposed A
+// operand.  Row tile (r, t):    A = pivot (transposed), B = own old values.
+// Column tile (t, r): A = own old values (transposed), B = pivot.
+// The product with the closed pivot equals the in-place sequential phases 2
+// and 3 (Sec. 2.3).  Predecessors are recorded as via codes (ViaPred), so the
+// task needs no predecessor tile.  The operand buffers are released right
+// after the relaxation: the producer streams the next task's operands while
+// this one stores its results.
+template <typename T, int BS, int LBS, bool is_row>
+__device__ __noinline__ bool ws_panel(const Args<T>& a, const fwh::Task& k, unsigned char* smem,
+                                      WsBars* wb, CtaScratch* cs, PipeCnt& pc) {
+  static_assert(Num<T>::kPacked, "producer-fed panels are the int32 path");
+  using Gm = Geo<BS>;
+  using K = Keys<BS>;
+  using L = WsLayout<LBS, T>;
+  static_assert(WsChunk<BS, T>::kTile <= L::kStage, "a tile per ring stage");
+  constexpr int TM = Gm::TM, G = Gm::G;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int r = k.r, t = is_row ? k.tj : k.ti;
+  const int64_t row0 = (int64_t)k.ti * BS, col0 = (int64_t)k.tj * BS;
+  const int nrow = (int)(a.n - row0 < BS ? a.n - row0 : BS);
+  const int ncol = (int)(a.n - col0 < BS ? a.n - col0 : BS);
+  T* Dbuf = reinterpret_cast<T*>(smem + L::d_off());
+  const unsigned s0 = pc.chunk & 1, s1 = s0 ^ 1;
+  T* Piv = reinterpret_cast<T*>(smem + L::ring_off() + s0 * L::kStage);
+  unsigned char* scratch = smem + L::ring_off() + s1 * L::kStage;
+  stamp(0);
+  if (!mbar_wait(&wb->d_full, pc.d & 1, a.status, a.abort_flag, a.timeout_ns) ||
+      !mbar_wait(&wb->chunk_full[s0], (pc.chunk >> 1) & 1, a.status, a.abort_flag,
+                 a.timeout_ns) ||
+      !mbar_wait(&wb->chunk_full[s1], ((pc.chunk + 1) >> 1) & 1, a.status, a.abort_flag,
+                 a.timeout_ns))
+    return false;
+
+  // micro-tiles of the tile (entries beyond n read as INF) and of the pivot
+  T s[TM][TM], pv[TM][TM];
+#pragma unroll
+  for (int m = 0; m < TM; ++m) {
+    const int lr = Gm::idx(ty, m);
+#pragma unroll
+    for (int g = 0; g < Gm::NG; ++g) {
+      const int lc0 = g * Gm::SPAN + tx * G;
+      T ts[G], tp[G];
+      vload_s<G>(ts, Dbuf + lr * BS + lc0);
+      vload_s<G>(tp, Piv + lr * BS + lc0);
+#pragma unroll
+      for (int e = 0; e < G; ++e) {
+        s[m][g * G + e] = (lr < nrow && lc0 + e < ncol) ? ts[e] : Num<T>::inf();
+        pv[m][g * G + e] = tp[e];
+      }
+    }
+  }
+  int bs_ = 0, bp_ = 0;
+#pragma unroll
+  for (int m = 0; m < TM; ++m)
+#pragma unroll
+    for (int nn = 0; nn < TM; ++nn) {
+      bs_ = max(bs_, bound_of<BS>(s[m][nn]));
+      bp_ = max(bp_, bound_of<BS>(pv[m][nn]));
+    }
+  block_max2(bs_, bp_, cs);  // (its barriers also end every read of the raw buffers)
+  const bool fast = a.packed && (bs_ + bp_ < K::CAP);
+
+  // operands: A (transposed) into the scratch stage, B in place (natural
+  // layout: the own tile in Dbuf for a row tile, the pivot for a column
+  // tile).  Keys are formed in the registers of s and pv (int32), so that the
+  // accumulators are only loaded once those are dead.
+  uint32_t* Bk = reinterpret_cast<uint32_t*>(is_row ? (void*)Dbuf : (void*)Piv);
+  if (fast) {
+    uint32_t (&ka)[TM][TM] = reinterpret_cast<uint32_t(&)[TM][TM]>(is_row ? pv : s);
+    uint32_t (&kb)[TM][TM] = reinterpret_cast<uint32_t(&)[TM][TM]>(is_row ? s : pv);
+#pragma unroll
+    for (int m = 0; m < TM; ++m)
+#pragma unroll
+      for (int nn = 0; nn < TM; ++nn) {
+        const uint32_t cc = (uint32_t)Gm::idx(tx, nn) + 1u;  // the A entry's kk + 1
+        ka[m][nn] = key_of<BS>((int32_t)ka[m][nn]) + cc;
+        kb[m][nn] = key_of<BS>((int32_t)kb[m][nn]);
+      }
+    put_tile<BS, true>(reinterpret_cast<uint32_t*>(scratch), ka, tx, ty);
+    put_tile<BS, false>(Bk, kb, tx, ty);
+  } else {
+    if constexpr (is_row) {
+      put_tile<BS, true>(reinterpret_cast<T*>(scratch), pv, tx, ty);
+      put_tile<BS, false>(Dbuf, s, tx, ty);  // (entries beyond n as INF)
+    } else {
+      put_tile<BS, true>(reinterpret_cast<T*>(scratch), s, tx, ty);
+    }
+  }
+  bar_compute();
+  stamp(1);
+  return fast ? ws_panel_finish<T, BS, LBS, is_row, true>(a, r, t, Dbuf, Piv, scratch, wb, cs, pc)
+              : ws_panel_finish<T, BS, LBS, is_row, false>(a, r, t, Dbuf, Piv, scratch, wb, cs,
+                                                           pc);
+}
+
 // Any task, compute-warp side.
 template <typename T, int BS, int LBS>
-__device__ bool compute_task(const Args<T>& a, const fwh::Task& k, bool fast, unsigned char* smem,
-                             WsBars* wb, CtaScratch* cs, PipeCnt& pc, uint64_t* tr) {
+__device__ bool compute_task(const Args<T>& a, const fwh::Task& k, bool fast, int dec,
+                             unsigned char* smem, WsBars* wb, CtaScratch* cs, PipeCnt& pc,
+                             uint64_t* tr) {
   using L = WsLayout<LBS, T>;
   if (k.type == 3) {
     const TileCtx<T> ctx{a.D, a.P, a.n, a.ld, k.r, a.status, a.abort_flag, a.timeout_ns};
-    return ws_minplus<T, BS, LBS>(ctx, k.ti, k.tj, fast, smem, wb, pc, tr);
+    return ws_minplus<T, BS, LBS>(ctx, k.ti, k.tj, fast, dec, smem, wb, pc, tr);
   }
-  // Pivot and panel tasks overwrite the ring and Dbuf from their first
-  // instructions: every compute warp must have left the previous task (a slow
-  // warp may still be reading its last operand chunk) before any warp starts.
+  if constexpr (Num<T>::kPacked) {
+    if (k.type != 0) {
+      const bool ok = k.type == 1 ? ws_panel<T, BS, LBS, true>(a, k, smem, wb, cs, pc)
+                                  : ws_panel<T, BS, LBS, false>(a, k, smem, wb, cs, pc);
+      if (ok && tr) {
+        const long long t0 = t_stamp[0], t_end = clock64();
+        tr[7] = (uint64_t)(t_stamp[1] - t0) | ((uint64_t)(t_stamp[2] - t0) << 32);
+        tr[8] = (uint64_t)(t_stamp[3] - t0) | ((uint64_t)(t_end - t0) << 32);
+      }
+      return ok;
+    }
+  }
+  // Pivot (and, for the other types, panel) tasks overwrite the ring and Dbuf
+  // from their first instructions: every compute warp must have left the
+  // previous task (a slow warp may still be reading its last operand chunk)
+  // before any warp starts.
   bar_compute();
   if (k.type == 0) {
     task_pivot<T, BS>(a, k.r, smem + L::ring_off(), cs);
@@ -537,14 +877,13 @@ __device__ __forceinline__ bool packed_ok(const Args<T>& a, const fwh::Task& k) 
   return ba + bb < Keys<BS>::CAP;
 }
 
-// Issue the operand copies of remaining-tile task k (whole producer warp).
+// Copy the tile (k.ti, k.tj) of D into Dbuf (whole producer warp): one 2-D
+// tensor copy, or one bulk copy per valid row.
 template <typename T, int BS, int LBS>
-__device__ void issue_operands(const Args<T>& a, const fwh::Task& k, bool fast, unsigned char* smem,
-                               WsBars* wb, PipeCnt& pc, int lane) {
+__device__ __forceinline__ void issue_tile_load(const Args<T>& a, const fwh::Task& k,
+                                                unsigned char* smem, WsBars* wb, PipeCnt& pc,
+                                                int lane) {
   using L = WsLayout<LBS, T>;
-  using C = WsChunk<BS, T>;
-  fence_proxy_async();  // global data published by other CTAs, read by TMA below
-  const int slot = k.r & 1;
   // the tile's own D block, one bulk copy per valid row
   const int64_t row0 = (int64_t)k.ti * BS, col0 = (int64_t)k.tj * BS;
   const int nrows = (int)(a.n - row0 < (int64_t)BS ? a.n - row0 : (int64_t)BS);
@@ -584,13 +923,36 @@ __device__ void issue_operands(const Args<T>& a, const fwh::Task& k, bool fast, 
                  &wb->d_full);
   }
   ++pc.d;
+}
+
+// Operand forms of a compare-and-select remaining tile (int32): the panel
+// snapshots it reads as keys (bit 0: A, bit 1: B) because their panels wrote
+// the exact keys only (bound below CAP, packed keys in use).
+template <typename T, int BS>
+__device__ __forceinline__ int key_operands(const Args<T>& a, const fwh::Task& k, bool fast) {
+  if (!(Num<T>::kPacked && a.packed && k.type == 3) || fast) return 0;
+  const int slot = k.r & 1;
+  const int ba = __ldcg(a.colB + (size_t)slot * a.slot_tiles + k.ti);
+  const int bb = __ldcg(a.rowB + (size_t)slot * a.slot_tiles + k.tj);
+  return (ba < Keys<BS>::CAP ? 1 : 0) | (bb < Keys<BS>::CAP ? 2 : 0);
+}
+
+// Issue the operand copies of remaining-tile task k (whole producer warp).
+template <typename T, int BS, int LBS>
+__device__ void issue_operands(const Args<T>& a, const fwh::Task& k, bool fast, int dec,
+                               unsigned char* smem, WsBars* wb, PipeCnt& pc, int lane) {
+  using L = WsLayout<LBS, T>;
+  using C = WsChunk<BS, T>;
+  fence_proxy_async();  // global data published by other CTAs, read by TMA below
+  const int slot = k.r & 1;
+  issue_tile_load<T, BS, LBS>(a, k, smem, wb, pc, lane);
   // operand chunks
   const size_t toffA = ((size_t)slot * a.slot_tiles + k.ti) * BS * BS;
   const size_t toffB = ((size_t)slot * a.slot_tiles + k.tj) * BS * BS;
-  const unsigned char* srcA = fast ? (const unsigned char*)(a.colK + toffA)
-                                   : (const unsigned char*)(a.colR + toffA);
-  const unsigned char* srcB = fast ? (const unsigned char*)(a.rowK + toffB)
-                                   : (const unsigned char*)(a.rowR + toffB);
+  const unsigned char* srcA = (fast || (dec & 1)) ? (const unsigned char*)(a.colK + toffA)
+                                                 : (const unsigned char*)(a.colR + toffA);
+  const unsigned char* srcB = (fast || (dec & 2)) ? (const unsigned char*)(a.rowK + toffB)
+                                                 : (const unsigned char*)(a.rowR + toffB);
   for (int c = 0; c < C::NC; ++c) {
     if (lane == 0) {
       const unsigned st = pc.chunk & 1;
@@ -621,6 +983,42 @@ __device__ void issue_operands(const Args<T>& a, const fwh::Task& k, bool fast, 
     }
     ++pc.p;
   }
+}
+
+// Issue the operands of panel task k (int32, whole producer warp): the tile
+// into Dbuf, the closed pivot of round k.r into the next ring stage, and the
+// stage after it handed over empty as the task's scratch (ws_panel).
+template <typename T, int BS, int LBS>
+__device__ void issue_panel_operands(const Args<T>& a, const fwh::Task& k, unsigned char* smem,
+                                     WsBars* wb, PipeCnt& pc, int lane) {
+  using L = WsLayout<LBS, T>;
+  using C = WsChunk<BS, T>;
+  fence_proxy_async();  // global data published by other CTAs, read by TMA below
+  issue_tile_load<T, BS, LBS>(a, k, smem, wb, pc, lane);
+  if (lane == 0) {
+    const unsigned st = pc.chunk & 1;
+    if (!pc.stop && mbar_wait(&wb->chunk_empty[st], ((pc.chunk >> 1) & 1) ^ 1, a.status,
+                              a.abort_flag, a.timeout_ns)) {
+      mbar_expect_tx(&wb->chunk_full[st], (unsigned)C::kTile);
+      bulk_g2s(smem + L::ring_off() + st * L::kStage, a.piv + (size_t)(k.r & 1) * BS * BS,
+               (unsigned)C::kTile, &wb->chunk_full[st]);
+      pc.chunk_armed[st] = pc.chunk + 1;
+    } else {
+      pc.stop = true;
+    }
+    const unsigned st1 = (pc.chunk + 1) & 1;
+    if (!pc.stop && mbar_wait(&wb->chunk_empty[st1], (((pc.chunk + 1) >> 1) & 1) ^ 1, a.status,
+                              a.abort_flag, a.timeout_ns)) {
+      mbar_arrive(&wb->chunk_full[st1]);  // no copy: the stage is scratch
+      // (recorded all the same: the final drain waits on the latest phase of
+      // each barrier, and a parity wait on an older one would never succeed
+      // once the barrier is two phases further)
+      pc.chunk_armed[st1] = pc.chunk + 2;
+    } else {
+      pc.stop = true;
+    }
+  }
+  pc.chunk += 2;
 }
 
 // Optional per-task trace (sampled tasks): 10 words per entry.
@@ -735,11 +1133,15 @@ __device__ void ws_engine(const Src& src, unsigned char* smem, WsBars& wb, CtaSc
         }
       }
       bool fast = false;
+      int dec = 0;
       int bs = 0;
       if (t >= 0) {
         bs = src.bs(g);
         fast = with_bs<kFixedBS, LBS>(bs, [&](auto B) {
           return packed_ok<T, decltype(B)::value>(src.args(g), k);
+        });
+        dec = with_bs<kFixedBS, LBS>(bs, [&](auto B) {
+          return key_operands<T, decltype(B)::value>(src.args(g), k, fast);
         });
       }
       unsigned pq = 0;
@@ -765,6 +1167,7 @@ __device__ void ws_engine(const Src& src, unsigned char* smem, WsBars& wb, CtaSc
         wb.desc[ds][4] = k.tj;
         wb.desc[ds][5] = fast ? 1 : 0;
         wb.desc[ds][6] = g;
+        wb.desc[ds][7] = dec;
         mbar_arrive(&wb.desc_full[ds]);
       }
       ++idesc;
@@ -772,7 +1175,13 @@ __device__ void ws_engine(const Src& src, unsigned char* smem, WsBars& wb, CtaSc
       if (t < 0) break;
       if (k.type == 3) {
         with_bs<kFixedBS, LBS>(bs, [&](auto B) {
-          issue_operands<T, decltype(B)::value, LBS>(src.args(g), k, fast, smem, &wb, pc, lane);
+          issue_operands<T, decltype(B)::value, LBS>(src.args(g), k, fast, dec, smem, &wb, pc,
+                                                     lane);
+          return 0;
+        });
+      } else if (Num<T>::kPacked && k.type != 0) {
+        with_bs<kFixedBS, LBS>(bs, [&](auto B) {
+          issue_panel_operands<T, decltype(B)::value, LBS>(src.args(g), k, smem, &wb, pc, lane);
           return 0;
         });
       } else {
@@ -789,7 +1198,7 @@ __device__ void ws_engine(const Src& src, unsigned char* smem, WsBars& wb, CtaSc
           tr[4] = globaltimer();
         }
       }
-      if (k.type != 3) fence_proxy_async();
+      if (k.type == 0 || (!Num<T>::kPacked && k.type != 3)) fence_proxy_async();
       __syncwarp();
     }
     // leave no bulk copy in flight: wait (bounded, whatever the abort flag
@@ -821,6 +1230,7 @@ __device__ void ws_engine(const Src& src, unsigned char* smem, WsBars& wb, CtaSc
     const fwh::Task k{wb.desc[ds][1], wb.desc[ds][2], wb.desc[ds][3], wb.desc[ds][4]};
     const bool fast = wb.desc[ds][5] != 0;
     const int g = wb.desc[ds][6];
+    const int dec = wb.desc[ds][7];
     __syncwarp();
     if (lane == 0) mbar_arrive(&wb.desc_empty[ds]);
     ++idesc;
@@ -828,7 +1238,8 @@ __device__ void ws_engine(const Src& src, unsigned char* smem, WsBars& wb, CtaSc
     uint64_t* tr = tid == 0 ? trace_slot(src.trace, src.trace_cap, src.trace_stride, t) : nullptr;
     if (tr) tr[6] = globaltimer();
     const bool ok = with_bs<kFixedBS, LBS>(src.bs(g), [&](auto B) {
-      return compute_task<T, decltype(B)::value, LBS>(src.args(g), k, fast, smem, &wb, &cs, pc, tr);
+      return compute_task<T, decltype(B)::value, LBS>(src.args(g), k, fast, dec, smem, &wb, &cs,
+                                                      pc, tr);
     });
     if (tr) tr[9] = globaltimer();
     if (!ok) break;

@@ -82,6 +82,28 @@ def test_int_mixed_bounds():
     check_int_full(W, D, P, Do, Po, cnt)
 
 
+@pytest.mark.parametrize("bs", [32, 64, 128])
+def test_int_key_only_snapshots(bs):
+    """Panel values between a quarter of the packed-key cap and above it:
+    panels whose values stay below the cap store their snapshot as keys only,
+    and remaining tiles whose two panels' bounds add up beyond the cap decode
+    those keys for the compare-and-select kernel; panels with larger values
+    store raw snapshots too (every combination within one solve)."""
+    n = 400
+    cap = (1 << (31 - {32: 6, 64: 7, 128: 8}[bs])) - 1
+    W = graphgen.dense_graph_i32(n, seed=bs, p=0.4, lo=1, hi=40)
+    big = graphgen.dense_graph_i32(n, seed=bs + 1, p=0.4, lo=cap // 4, hi=cap // 2)
+    W[:, 250:] = np.where(W[:, 250:] < INF, big[:, 250:], INF)
+    W[300:, :] = np.where(W[300:, :] < INF, np.maximum(W[300:, :], cap // 3), INF)
+    W[370:, :] = np.where(W[370:, :] < INF, cap + W[370:, :] % 1000, INF)
+    np.fill_diagonal(W, 0)
+    Do, Po = oracle.fw_i64(W)
+    assert Do[Do < INF].max() > cap  # some values beyond the cap
+    cnt = oracle.path_count_i64(W, Do)
+    D, P = gpu_solve(W, bs=bs)
+    check_int_full(W, D, P, Do, Po, cnt)
+
+
 def test_int_padding_untouched_and_disconnected():
     n = 150
     W = graphgen.dense_graph_i32(n, seed=3, p=0.2, lo=1, hi=9)
