@@ -1173,6 +1173,16 @@ __device__ __forceinline__ int panel_store_group(const Args<T>& a, int r, int t,
   const int ti = is_row ? r : t, tj = is_row ? t : r;
   const int slot = r & 1;
   const size_t tile_off = ((size_t)slot * a.slot_tiles + t) * BS * BS;
+  // pointers and sizes in registers: read through the reference they would
+  // be reloaded after every store (which might alias them)
+  T* const D = a.D;
+  int32_t* const P = a.P;
+  const int64_t n = a.n, ld = a.ld;
+  T* const rowR = a.rowR + tile_off;
+  int32_t* const rowP = a.rowP + tile_off;
+  uint32_t* const rowK = a.rowK + tile_off;
+  T* const colR = a.colR;
+  uint32_t* const colK = a.colK;
   int nb = 0;
 #pragma unroll
   for (int e = 0; e < G; ++e) {
@@ -1190,46 +1200,46 @@ __device__ __forceinline__ int panel_store_group(const Args<T>& a, int r, int t,
         vp[q] = np[e][gg * G + q];
         if constexpr (Num<T>::kPacked) nb = max(nb, bound_of<BS>(vs[q]));
       }
-      if (gi < a.n) {
-        if (gj0 + G <= a.n) {
-          vstore<G>(a.D + gi * a.ld + gj0, vs);
-          if (!a.P) {
+      if (gi < n) {
+        if (gj0 + G <= n) {
+          vstore<G>(D + gi * ld + gj0, vs);
+          if (!P) {
             // distance-only
           } else if constexpr (is_row && !kSparseP) {
-            vstore<G>(a.P + gi * a.ld + gj0, vp);
+            vstore<G>(P + gi * ld + gj0, vp);
           } else {
             bool all = true;
 #pragma unroll
             for (int q = 0; q < G; ++q) all &= imp[e][gg * G + q];
             if (all) {
-              vstore<G>(a.P + gi * a.ld + gj0, vp);  // (early rounds: most groups)
+              vstore<G>(P + gi * ld + gj0, vp);  // (early rounds: most groups)
             } else {
 #pragma unroll
               for (int q = 0; q < G; ++q)
-                if (imp[e][gg * G + q]) a.P[gi * a.ld + gj0 + q] = vp[q];
+                if (imp[e][gg * G + q]) P[gi * ld + gj0 + q] = vp[q];
             }
           }
         } else {
 #pragma unroll
           for (int q = 0; q < G; ++q)
-            if (gj0 + q < a.n) {
-              a.D[gi * a.ld + gj0 + q] = vs[q];
-              if (a.P && ((is_row && !kSparseP) || imp[e][gg * G + q]))
-                a.P[gi * a.ld + gj0 + q] = vp[q];
+            if (gj0 + q < n) {
+              D[gi * ld + gj0 + q] = vs[q];
+              if (P && ((is_row && !kSparseP) || imp[e][gg * G + q]))
+                P[gi * ld + gj0 + q] = vp[q];
             }
         }
       }
       if constexpr (is_row) {
         // B-form snapshots: raw, pred and packed key (code bits zero)
-        vstore<G>(a.rowR + tile_off + lr * BS + lc0, vs);
+        vstore<G>(rowR + lr * BS + lc0, vs);
         if constexpr (!ViaPred<T>::kOn) {
-          if (a.P) vstore<G>(a.rowP + tile_off + lr * BS + lc0, vp);
+          if (P) vstore<G>(rowP + lr * BS + lc0, vp);
         }
         if constexpr (Num<T>::kPacked) {
           uint32_t kq[G];
 #pragma unroll
           for (int q = 0; q < G; ++q) kq[q] = key_of<BS>((int32_t)vs[q]);
-          vstore<G>(a.rowK + tile_off + lr * BS + lc0, kq);
+          vstore<G>(rowK + lr * BS + lc0, kq);
         }
       }
     }
@@ -1243,12 +1253,12 @@ __device__ __forceinline__ int panel_store_group(const Args<T>& a, int r, int t,
       T vs[G];
 #pragma unroll
       for (int e = 0; e < G; ++e) vs[e] = sv[e][nn];
-      vstore<G>(a.colR + off, vs);
+      vstore<G>(colR + off, vs);
       if constexpr (Num<T>::kPacked) {
         uint32_t kq[G];
 #pragma unroll
         for (int e = 0; e < G; ++e) kq[e] = key_of<BS>((int32_t)vs[e]) + (uint32_t)lc + 1u;
-        vstore<G>(a.colK + off, kq);
+        vstore<G>(colK + off, kq);
       }
     }
   }

@@ -555,6 +555,14 @@ __device__ __noinline__ bool ws_panel_finish(const Args<T>& a, int r, int t, T* 
   const bool raw = !keys || nb >= K::CAP;
   const int slot = r & 1;
   const size_t tile_off = ((size_t)slot * a.slot_tiles + t) * BS * BS;
+  // the pointers and sizes in registers: through the reference every access
+  // would be a load, repeated after each store (which might alias it)
+  T* const D = a.D;
+  int32_t* const P = a.P;
+  const int64_t n = a.n, ld = a.ld;
+  uint32_t* const snapK = (is_row ? a.rowK : a.colK) + tile_off;
+  T* const snapR = (is_row ? a.rowR : a.colR) + tile_off;
+  int32_t* const bnd = (is_row ? a.rowB : a.colB) + (size_t)slot * a.slot_tiles + t;
 
   // the live tile (values, and via codes k = r*BS + code - 1 where improved);
   // a row tile's snapshots in the same (B-form) order
@@ -579,24 +587,24 @@ __device__ __noinline__ bool ws_panel_finish(const Args<T>& a, int r, int t, T* 
         vp[q] = via0 - cq[q];
         all &= cq[q] != 0;
       }
-      if (gi < a.n) {
-        if (gj0 + G <= a.n) {
-          vstore<G>(a.D + gi * a.ld + gj0, vs);
-          if (a.P) {
+      if (gi < n) {
+        if (gj0 + G <= n) {
+          vstore<G>(D + gi * ld + gj0, vs);
+          if (P) {
             if (all) {
-              vstore<G>(a.P + gi * a.ld + gj0, vp);  // (early rounds: most groups)
+              vstore<G>(P + gi * ld + gj0, vp);  // (early rounds: most groups)
             } else {
 #pragma unroll
               for (int q = 0; q < G; ++q)
-                if (cq[q]) a.P[gi * a.ld + gj0 + q] = vp[q];
+                if (cq[q]) P[gi * ld + gj0 + q] = vp[q];
             }
           }
         } else {
 #pragma unroll
           for (int q = 0; q < G; ++q)
-            if (gj0 + q < a.n) {
-              a.D[gi * a.ld + gj0 + q] = vs[q];
-              if (a.P && cq[q]) a.P[gi * a.ld + gj0 + q] = vp[q];
+            if (gj0 + q < n) {
+              D[gi * ld + gj0 + q] = vs[q];
+              if (P && cq[q]) P[gi * ld + gj0 + q] = vp[q];
             }
         }
       }
@@ -605,9 +613,9 @@ __device__ __noinline__ bool ws_panel_finish(const Args<T>& a, int r, int t, T* 
           uint32_t kq[G];
 #pragma unroll
           for (int q = 0; q < G; ++q) kq[q] = key(m, gg * G + q);
-          vstore<G>(a.rowK + tile_off + lr * BS + lc0, kq);
+          vstore<G>(snapK + lr * BS + lc0, kq);
         }
-        if (raw) vstore<G>(a.rowR + tile_off + lr * BS + lc0, vs);
+        if (raw) vstore<G>(snapR + lr * BS + lc0, vs);
       }
     }
   }
@@ -618,26 +626,23 @@ __device__ __noinline__ bool ws_panel_finish(const Args<T>& a, int r, int t, T* 
       const int lc = Gm::idx(tx, nn);
 #pragma unroll
       for (int g = 0; g < Gm::NG; ++g) {
-        const size_t off = tile_off + (size_t)lc * BS + g * Gm::SPAN + ty * G;
+        const size_t off = (size_t)lc * BS + g * Gm::SPAN + ty * G;
         if (keys) {
           uint32_t kq[G];
 #pragma unroll
           for (int e = 0; e < G; ++e) kq[e] = key(g * G + e, nn) + (uint32_t)lc + 1u;
-          vstore<G>(a.colK + off, kq);
+          vstore<G>(snapK + off, kq);
         }
         if (raw) {
           T vs[G];
 #pragma unroll
           for (int e = 0; e < G; ++e) vs[e] = value(g * G + e, nn);
-          vstore<G>(a.colR + off, vs);
+          vstore<G>(snapR + off, vs);
         }
       }
     }
   }
-  if (tid == 0) {
-    int32_t* bnd = is_row ? a.rowB : a.colB;
-    bnd[(size_t)slot * a.slot_tiles + t] = nb;
-  }
+  if (tid == 0) *bnd = nb;
   stamp(3);
   return true;
 }
