@@ -34,6 +34,13 @@ namespace fwk {
 // thread (ptxas derives this from the launch bounds).
 constexpr int kWsThreads = kThreads + 64;
 constexpr int kPubDepth = 4;  // tasks handed to the compute warps but not yet published
+// Internal task type: remaining tile (r+1, r+1) of round r followed, on the
+// same CTA and without a publication in between, by the pivot of round r+1
+// (whose own queue entry is then skipped).  That tile is the pivot's only
+// input, so the pivot starts as soon as the tile is relaxed: one hand-off
+// less on the chain that bounds small solves (pivot -> panels -> tile ->
+// next pivot).
+constexpr int kFusedTask = 4;
 
 // Operand chunks of a task with block size BS: CK k-steps of A and of B.
 // int32 streams 64-step chunks (2 per task at BS = 128: fewer ring hand-offs);
@@ -751,9 +758,17 @@ __device__ bool compute_task(const Args<T>& a, const fwh::Task& k, bool fast, in
                              unsigned char* smem, WsBars* wb, CtaScratch* cs, PipeCnt& pc,
                              uint64_t* tr) {
   using L = WsLayout<LBS, T>;
-  if (k.type == 3) {
+  if (k.type == 3 || k.type == kFusedTask) {
     const TileCtx<T> ctx{a.D, a.P, a.n, a.ld, k.r, a.status, a.abort_flag, a.timeout_ns};
-    return ws_minplus<T, BS, LBS>(ctx, k.ti, k.tj, fast, dec, smem, wb, pc, tr);
+    const bool ok = ws_minplus<T, BS, LBS>(ctx, k.ti, k.tj, fast, dec, smem, wb, pc, tr);
+    if (!ok || k.type == 3) return ok;
+    // fused: the tile's stores precede the pivot's loads of it (same CTA),
+    // and every warp has left the tile's operand buffers before the pivot
+    // reuses them
+    bar_compute();
+    task_pivot<T, BS>(a, k.r + 1, smem + L::ring_off(), cs);
+    bar_compute();
+    return true;
   }
   if constexpr (Num<T>::kPacked) {
     if (k.type != 0) {
@@ -844,6 +859,13 @@ __device__ __forceinline__ bool dep_of(const Args<T>& a, const fwh::Task& k, int
       if (lane == 0) { p = ver + (size_t)k.ti * R + k.tj; target = k.r; return true; }
       if (lane == 1) { p = ver + (size_t)k.ti * R + k.r; target = k.r + 1; return true; }
       if (lane == 2) { p = ver + (size_t)k.r * R + k.tj; target = k.r + 1; return true; }
+      // tile (r+1, r+1) fused with the pivot of round r+1: that pivot's
+      // snapshot slot is free once every panel of round r-1 is done
+      if (lane == 3 && k.type == kFusedTask && k.r >= 1) {
+        p = a.done + (k.r - 1);
+        target = 2 * (R - 1);
+        return true;
+      }
       return false;
   }
 }
@@ -856,7 +878,7 @@ __device__ bool wait_deps(const Args<T>& a, const fwh::Task& k, int lane) {
   const int* p = nullptr;
   int target = 0;
   bool ok = true;
-  if (lane < 3 && dep_of(a, k, lane, p, target))
+  if (lane < 4 && dep_of(a, k, lane, p, target))
     ok = wait_ge(p, target, a.abort_flag, a.status, a.timeout_ns);
   return __all_sync(0xffffffffu, ok);
 }
@@ -867,15 +889,17 @@ __device__ bool wait_deps(const Args<T>& a, const fwh::Task& k, int lane) {
 // task_done mbarrier) visible to whoever acquires the flag.
 template <typename T>
 __device__ __forceinline__ void publish(const Args<T>& a, const fwh::Task& k) {
-  st_release(a.ver + (size_t)k.ti * a.R + k.tj, k.r + 1);
+  // (a fused task publishes its tile after round r+1's pivot: version r+2)
+  st_release(a.ver + (size_t)k.ti * a.R + k.tj, k.type == kFusedTask ? k.r + 2 : k.r + 1);
   if (k.type == 1 || k.type == 2) red_release_add(reinterpret_cast<unsigned*>(a.done + k.r), 1u);
-  if (k.type == 3) red_release_add(reinterpret_cast<unsigned*>(a.done + a.R + k.r), 1u);
+  if (k.type == 3 || k.type == kFusedTask)
+    red_release_add(reinterpret_cast<unsigned*>(a.done + a.R + k.r), 1u);
 }
 
 // Whether a remaining-tile task may relax packed keys (int32, bounded panels).
 template <typename T, int BS>
 __device__ __forceinline__ bool packed_ok(const Args<T>& a, const fwh::Task& k) {
-  if (!(Num<T>::kPacked && a.packed && k.type == 3)) return false;
+  if (!(Num<T>::kPacked && a.packed && (k.type == 3 || k.type == kFusedTask))) return false;
   const int slot = k.r & 1;
   const int ba = __ldcg(a.colB + (size_t)slot * a.slot_tiles + k.ti);
   const int bb = __ldcg(a.rowB + (size_t)slot * a.slot_tiles + k.tj);
@@ -935,7 +959,7 @@ __device__ __forceinline__ void issue_tile_load(const Args<T>& a, const fwh::Tas
 // the exact keys only (bound below CAP, packed keys in use).
 template <typename T, int BS>
 __device__ __forceinline__ int key_operands(const Args<T>& a, const fwh::Task& k, bool fast) {
-  if (!(Num<T>::kPacked && a.packed && k.type == 3) || fast) return 0;
+  if (!(Num<T>::kPacked && a.packed && (k.type == 3 || k.type == kFusedTask)) || fast) return 0;
   const int slot = k.r & 1;
   const int ba = __ldcg(a.colB + (size_t)slot * a.slot_tiles + k.ti);
   const int bb = __ldcg(a.rowB + (size_t)slot * a.slot_tiles + k.tj);
@@ -1128,6 +1152,10 @@ __device__ void ws_engine(const Src& src, unsigned char* smem, WsBars& wb, CtaSc
       k.ti = __shfl_sync(0xffffffffu, k.ti, 0);
       k.tj = __shfl_sync(0xffffffffu, k.tj, 0);
       if (t >= 0) {
+        // tile (r+1, r+1) of round r takes the pivot of round r+1 along, and
+        // that pivot's own queue entry is skipped
+        if (k.type == 0 && k.r >= 1) continue;
+        if (k.type == 3 && k.ti == k.r + 1 && k.tj == k.r + 1) k.type = kFusedTask;
         if (!wait_deps(src.args(g), k, lane)) t = -1;
       }
       if (lane == 0) {
@@ -1178,12 +1206,18 @@ __device__ void ws_engine(const Src& src, unsigned char* smem, WsBars& wb, CtaSc
       ++idesc;
       ++ipub;
       if (t < 0) break;
-      if (k.type == 3) {
+      if (k.type == 3 || k.type == kFusedTask) {
         with_bs<kFixedBS, LBS>(bs, [&](auto B) {
           issue_operands<T, decltype(B)::value, LBS>(src.args(g), k, fast, dec, smem, &wb, pc,
                                                      lane);
           return 0;
         });
+        if (k.type == kFusedTask && lane == 0) {
+          // its pivot uses the shared buffer as scratch: wait until the task
+          // has been published (its publication-queue slot frees up)
+          mbar_wait(&wb.pub_empty[pq], (((ipub - 1) / kPubDepth) & 1), src.status,
+                    src.abort_flag, src.timeout_ns);
+        }
       } else if (Num<T>::kPacked && k.type != 0) {
         with_bs<kFixedBS, LBS>(bs, [&](auto B) {
           issue_panel_operands<T, decltype(B)::value, LBS>(src.args(g), k, smem, &wb, pc, lane);
@@ -1203,7 +1237,8 @@ __device__ void ws_engine(const Src& src, unsigned char* smem, WsBars& wb, CtaSc
           tr[4] = globaltimer();
         }
       }
-      if (k.type == 0 || (!Num<T>::kPacked && k.type != 3)) fence_proxy_async();
+      if (k.type == 0 || k.type == kFusedTask || (!Num<T>::kPacked && k.type != 3))
+        fence_proxy_async();
       __syncwarp();
     }
     // leave no bulk copy in flight: wait (bounded, whatever the abort flag

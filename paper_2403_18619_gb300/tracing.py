@@ -7,13 +7,16 @@ compute warps started and finished it, and when it was published.  The buffer
 (``trace_cap`` rows of 10 uint64, filled on the device; include/fw.h) holds:
 
   [0] task index | type << 32 | graph << 40   (type: 0 pivot, 1 row panel,
-      2 column panel, 3 remaining tile; graph: the graph of a batched solve)
+      2 column panel, 3 remaining tile, 4 remaining tile (r+1, r+1) of round
+      r followed on the same SM by the pivot of round r+1, whose own queue
+      entry is then skipped; graph: the graph of a batched solve)
   [1] SM id
   [2] claimed  [3] inputs ready  [4] operands issued  [5] published   (%globaltimer, ns)
   [6] compute start  [9] compute end                                  (%globaltimer, ns)
   [7] [8] SM-cycle counts of the task's phases:
       remaining tile: [7] = tile-load wait | chunk waits << 20 | predecessor-tile
                       wait << 40 (20 bits each), [8] = relaxation end | whole << 32
+                      (type 4: of its tile part)
       pivot / panel:  [7] = operands loaded | relaxed << 32,
                       [8] = results stored | whole << 32
 
@@ -23,7 +26,7 @@ from __future__ import annotations
 
 import numpy as np
 
-TYPES = ("pivot", "row_panel", "col_panel", "remaining")
+TYPES = ("pivot", "row_panel", "col_panel", "remaining", "tile_pivot")
 
 
 def decode(trace) -> dict:
@@ -90,7 +93,7 @@ def summarize(trace) -> dict:
             continue
         e = {"compute_us": _stats(comp[m]), "input_wait_us": _stats(wait[m]),
              "publish_lag_us": _stats(lag[m])}
-        if ty == 3:
+        if ty in (3, 4):
             relax = d["relax_end"][m] - d["tile_wait"][m] - d["chunk_wait"][m]
             e["cycles"] = {
                 "tile_wait": float(d["tile_wait"][m].mean()),
@@ -140,7 +143,7 @@ def summarize_batched(trace, ns, bs_per_graph, bounds=(128, 256, 512, 1024, 2048
     wait = (d["ready"] - d["claimed"]).astype(np.float64) / 1e3
     total = comp.sum()
     out["compute_share_by_type"] = {TYPES[t]: float(comp[d["type"] == t].sum() / total)
-                                    for t in range(4) if (d["type"] == t).any()}
+                                    for t in range(len(TYPES)) if (d["type"] == t).any()}
     by = {}
     for c in np.unique(cls):
         m = cls == c
@@ -149,7 +152,7 @@ def summarize_batched(trace, ns, bs_per_graph, bounds=(128, 256, 512, 1024, 2048
         e = {"graphs": int(g.size), "bs": sorted(set(int(x) for x in bsg[g])),
              "compute_share": float(comp[m].sum() / total),
              "span_us": float((d["published"][m].max() - d["claimed"][m].min()) / 1e3)}
-        for t in range(4):
+        for t in range(len(TYPES)):
             mt = m & (d["type"] == t)
             if mt.any():
                 e[TYPES[t]] = {"tasks": int(mt.sum()), "compute_us": float(comp[mt].mean()),
@@ -177,7 +180,12 @@ def critical_path(trace, queue) -> dict:
       to_tile    to the remaining tile's compute start
       tile       its compute          tile_pub   its publication
       to_pivot   to pivot(r+1)'s compute start
-    and their sum, the round time along the chain."""
+    and their sum, the round time along the chain.  When the engine fuses
+    tile (r+1, r+1) with pivot(r+1) (trace type 4), a round r >= 1 runs from
+    the fused task of round r-1 to that of round r:
+      tile_pivot  compute of tile (r, r) of round r-1 and of pivot(r)
+      pivot_pub, to_panels, panels, panel_pub  as above
+      to_tile     to the next fused task's compute start"""
     d = decode(trace)
     q = np.asarray(queue)
     key = {(int(t), int(r), int(i), int(j)): k for k, (t, r, i, j) in enumerate(q)}
@@ -187,22 +195,37 @@ def critical_path(trace, queue) -> dict:
         k = key.get((typ, r, i, j))
         return row.get(k) if k is not None else None
 
-    names = ("pivot", "pivot_pub", "to_panels", "panels", "panel_pub", "to_tile", "tile",
-             "tile_pub", "to_pivot")
-    segs = {k: [] for k in names}
+    st, en, pb = d["start"], d["end"], d["published"]
     R = int(q[:, 1].max()) + 1 if len(q) else 0
-    for r in range(R - 1):
-        ids = [get(0, r, r, r), get(1, r, r, r + 1), get(2, r, r + 1, r), get(3, r, r + 1, r + 1),
-               get(0, r + 1, r + 1, r + 1)]
-        if any(x is None for x in ids):
-            continue
-        pv, prow, pcol, tl, nx = ids
-        st, en, pb = d["start"], d["end"], d["published"]
-        t = [st[pv], en[pv], pb[pv], max(st[prow], st[pcol]), max(en[prow], en[pcol]),
-             max(pb[prow], pb[pcol]), st[tl], en[tl], pb[tl], st[nx]]
-        for k, a, b in zip(names, t[:-1], t[1:]):
-            segs[k].append((b - a) / 1e3)
-    out = {"rounds": len(segs["pivot"])}
+    fused = bool((d["type"] == 4).any())
+    if fused:
+        names = ("tile_pivot", "pivot_pub", "to_panels", "panels", "panel_pub", "to_tile")
+        segs = {k: [] for k in names}
+        for r in range(1, R - 1):
+            ids = [get(3, r - 1, r, r), get(1, r, r, r + 1), get(2, r, r + 1, r),
+                   get(3, r, r + 1, r + 1)]
+            if any(x is None for x in ids):
+                continue
+            fp, prow, pcol, nx = ids
+            t = [st[fp], en[fp], pb[fp], max(st[prow], st[pcol]), max(en[prow], en[pcol]),
+                 max(pb[prow], pb[pcol]), st[nx]]
+            for k, a, b in zip(names, t[:-1], t[1:]):
+                segs[k].append((b - a) / 1e3)
+    else:
+        names = ("pivot", "pivot_pub", "to_panels", "panels", "panel_pub", "to_tile", "tile",
+                 "tile_pub", "to_pivot")
+        segs = {k: [] for k in names}
+        for r in range(R - 1):
+            ids = [get(0, r, r, r), get(1, r, r, r + 1), get(2, r, r + 1, r),
+                   get(3, r, r + 1, r + 1), get(0, r + 1, r + 1, r + 1)]
+            if any(x is None for x in ids):
+                continue
+            pv, prow, pcol, tl, nx = ids
+            t = [st[pv], en[pv], pb[pv], max(st[prow], st[pcol]), max(en[prow], en[pcol]),
+                 max(pb[prow], pb[pcol]), st[tl], en[tl], pb[tl], st[nx]]
+            for k, a, b in zip(names, t[:-1], t[1:]):
+                segs[k].append((b - a) / 1e3)
+    out = {"rounds": len(segs[names[0]]), "fused": fused}
     if out["rounds"]:
         means = {k: float(np.mean(v)) for k, v in segs.items()}
         out["segments_us"] = means

@@ -147,15 +147,22 @@ def test_task_trace_covers_every_task_in_order():
     m.fw_sync_status()
     check_int_full(W, D.cpu().numpy(), P.cpu().numpy(), Do, Po, cnt)
     d = tracing.decode(tr.cpu().numpy())
-    assert sorted(d["task"].tolist()) == list(range(R ** 3))
-    counts = np.bincount(d["type"], minlength=4).tolist()
-    assert counts == [R, R * (R - 1), R * (R - 1), R * (R - 1) ** 2]
+    # every task of the queue but the pivots of rounds 1..R-1, which run
+    # inside the task of tile (r, r) of round r-1 (trace type 4)
+    q = m.fw_queue_tasks(R, m.fw_solve_plan(n, m.Options.default(bs=bs))["lookahead"])
+    skipped = {k for k, (typ, r, i, j) in enumerate(q.tolist()) if typ == 0 and r >= 1}
+    fused = {k for k, (typ, r, i, j) in enumerate(q.tolist())
+             if typ == 3 and i == r + 1 and j == r + 1}
+    assert sorted(d["task"].tolist()) == sorted(set(range(R ** 3)) - skipped)
+    assert {t for t, ty in zip(d["task"].tolist(), d["type"].tolist()) if ty == 4} == fused
+    counts = np.bincount(d["type"], minlength=5).tolist()
+    assert counts == [1, R * (R - 1), R * (R - 1), R * (R - 1) ** 2 - (R - 1), R - 1]
     assert (d["claimed"] <= d["ready"]).all()
     assert (d["ready"] <= d["start"]).all()
     assert (d["start"] <= d["end"]).all()
     assert (d["end"] <= d["published"]).all()
     s = tracing.summarize(tr.cpu().numpy())
-    assert s["tasks"] == R ** 3 and 0 < s["busy_fraction"]["mean"] <= 1
+    assert s["tasks"] == R ** 3 - (R - 1) and 0 < s["busy_fraction"]["mean"] <= 1
 
 
 def test_repeated_solves_share_workspace():

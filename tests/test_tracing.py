@@ -115,3 +115,31 @@ def test_critical_path_segments():
     assert s["to_tile"] == pytest.approx(0.6) and s["tile"] == pytest.approx(1.0)
     assert s["tile_pub"] == pytest.approx(0.1) and s["to_pivot"] == pytest.approx(0.9)
     assert cp["round_us"] == pytest.approx(9.0)      # 1.0 -> 10.0
+
+
+def test_critical_path_fused_tile_and_pivot():
+    """Rounds of a solve whose tile (r+1, r+1) carries the pivot of round r+1
+    along (trace type 4, the pivot's own queue entry never traced): a round
+    runs from one fused task to the next."""
+    # queue rows of R = 3 (task ids by position); only the chain's tasks matter
+    q = [(0, 0, 0, 0), (1, 0, 0, 1), (2, 0, 1, 0), (3, 0, 1, 1), (0, 1, 1, 1),
+         (1, 1, 1, 2), (2, 1, 2, 1), (3, 1, 2, 2), (0, 2, 2, 2)]
+    rows = [
+        _row(3, 4, 0, 0, 0, 0, 1000, 4000, 4300),     # tile (1,1) of round 0 + pivot(1)
+        _row(5, 1, 1, 0, 0, 0, 5000, 6000, 6100),     # row panel (1,2)
+        _row(6, 2, 2, 0, 0, 0, 5200, 6500, 6800),     # column panel (2,1), the later one
+        _row(7, 4, 3, 0, 0, 0, 7500, 9000, 9200),     # tile (2,2) of round 1 + pivot(2)
+    ]
+    t = np.zeros((9, 10), np.uint64)
+    t[:4] = np.array(rows, dtype=np.uint64)
+    t[:4, 2] = 1
+    cp = tracing.critical_path(t, q)
+    assert cp["fused"] and cp["rounds"] == 1
+    s = cp["segments_us"]
+    assert s["tile_pivot"] == pytest.approx(3.0) and s["pivot_pub"] == pytest.approx(0.3)
+    assert s["to_panels"] == pytest.approx(0.9)       # 4.3 -> 5.2
+    assert s["panels"] == pytest.approx(1.3)          # 5.2 -> 6.5
+    assert s["panel_pub"] == pytest.approx(0.3) and s["to_tile"] == pytest.approx(0.7)
+    assert cp["round_us"] == pytest.approx(6.5)       # 1.0 -> 7.5
+    summary = tracing.summarize(t)
+    assert "tile_pivot" in summary["types"]
