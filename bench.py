@@ -335,6 +335,8 @@ def bench_backward(fw, args):
     import graphgen.device as gdev
     from paper_2403_18619_gb300.autograd import clear_plan_cache, shortest_paths
     B, n = 64, 1024
+    # the fp32 block sizes of this GPU (size classes up to n)
+    bs_table, _ = fw.fw_autotune_bs(fw.FW_F32, graphs_per_class=16, max_n=n)
     W = torch.empty((B, n, n), dtype=torch.float32, device="cuda")
     for b in range(B):
         gdev.fill_f32(W[b], seed=500 + b, p=0.1, kind=1)
@@ -400,6 +402,7 @@ def bench_backward(fw, args):
     hbm, src = _peaks()
     algo = float(B) * n * n * BWD_BYTES_PER_ENTRY
     return {"workload": "64 digraphs, n=1024, p=0.1, fp32 U[1,2), dL/dD ~ N(0,1)",
+            "bs_table_f32": bs_table.tolist(),
             "bwd_ms": bwd, "fwd_ms": fwd, "fwd_bwd_ms": fwd + bwd,
             "bwd_roofline": {"bound": "hbm", "algorithmic_bytes": algo,
                              "bytes_per_entry": BWD_BYTES_PER_ENTRY,

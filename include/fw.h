@@ -189,18 +189,22 @@ fw_status fw_batched_plan_info(const fw_batched_plan* plan, int32_t* bs_per_grap
 fw_status fw_batched_plan_destroy(fw_batched_plan* plan);
 
 /*
- * Block-size table of the batched planner (used when opt->bs == 0): one entry
- * per size class n <= 128, 256, 512, 1024, 2048, 4096, larger (7 entries),
- * each 32, 64 or 128.  set != 0 writes `table`, set == 0 reads it into `table`.
- * The paper's BS sweep (Sec. 4, Tables 2-3) is the motivation: the best block
- * size depends on the problem size.
+ * Block-size table of the batched planner for element type dtype (FW_I32 or
+ * FW_F32; used when opt->bs == 0): one entry per size class n <= 128, 256,
+ * 512, 1024, 2048, 4096, larger (7 entries), each 32, 64 or 128.  set != 0
+ * writes `table`, set == 0 reads it into `table`.  The paper's BS sweep
+ * (Sec. 4, Tables 2-3) is the motivation: the best block size depends on the
+ * problem size (and here on the element type).  The defaults are
+ * fw_autotune_bs's choices on a GB300.  FW_ERR_ARG for a null table, another
+ * dtype or an entry outside {32, 64, 128}; FW_ERR_UNSUPPORTED for the 64-bit
+ * types (no batched path).
  */
-fw_status fw_bs_table(int32_t* table, int32_t set);
+fw_status fw_bs_table(fw_dtype dtype, int32_t* table, int32_t set);
 
 /*
  * fw_autotune_bs: measures, for every size class up to max_n, a batched solve
  * of graphs_per_class synthetic graphs of the class's largest size with BS =
- * 32, 64 and 128, stores the fastest BS of each class in the table and copies
+ * 32, 64 and 128, stores the fastest BS of each class in dtype's table and copies
  * the table to table_out (7 entries) and the best times in ms to ms_out (may
  * be NULL).  Classes above max_n keep their entries.  Synchronous; allocates
  * its own inputs.

@@ -113,7 +113,7 @@ def load():
                                         I64, I32, P]
         lib.fw_block_init_pred.argtypes = [P, P, I64, I64, I64, I32, I64, I64, I64, I64, I64,
                                            I32, P]
-        lib.fw_bs_table.argtypes = [P, I32]
+        lib.fw_bs_table.argtypes = [I32, P, I32]
         lib.fw_autotune_bs.argtypes = [I32, I64, I64, P, P, P]
         for name in ("fw_solve", "fw_solve_ex", "fw_solve_host", "fw_batched_plan_create",
                      "fw_solve_batched", "fw_batched_plan_info", "fw_batched_plan_destroy",
@@ -454,10 +454,10 @@ class BatchedPlan:
             pass
 
 
-def fw_bs_table(table=None) -> np.ndarray:
-    """Read (table=None) or set the 7-entry per-size-class block-size table."""
+def fw_bs_table(table=None, dtype: int = FW_I32) -> np.ndarray:
+    """Read (table=None) or set dtype's 7-entry per-size-class block-size table."""
     t = np.zeros(7, np.int32) if table is None else np.ascontiguousarray(table, np.int32)
-    check(load().fw_bs_table(t.ctypes.data, 0 if table is None else 1), "fw_bs_table")
+    check(load().fw_bs_table(dtype, t.ctypes.data, 0 if table is None else 1), "fw_bs_table")
     return t
 
 

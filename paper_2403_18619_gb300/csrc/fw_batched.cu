@@ -115,8 +115,13 @@ namespace {
 constexpr int kClasses = 7;  // n <= 128, 256, 512, 1024, 2048, 4096, larger
 const int64_t kClassMax[kClasses] = {128, 256, 512, 1024, 2048, 4096, 1 << 30};
 
+// One table per element type (int32, fp32): the defaults are fw_autotune_bs's
+// choices on GB300 (16 graphs per class); packed int32 keys favour BS = 128
+// down to the smallest class, fp32's three-instruction relaxation BS = 32.
 std::mutex g_table_mu;
-int g_bs_table[kClasses] = {32, 32, 64, 64, 128, 128, 128};
+int g_bs_table[2][kClasses] = {{128, 64, 64, 128, 128, 128, 128},
+                               {32, 64, 64, 128, 128, 128, 128}};
+int table_index(fw_dtype dt) { return dt == FW_F32 ? 1 : 0; }
 
 int class_of(int64_t n) {
   for (int c = 0; c < kClasses; ++c)
@@ -124,9 +129,9 @@ int class_of(int64_t n) {
   return kClasses - 1;
 }
 
-int table_bs(int64_t n) {
+int table_bs(int64_t n, fw_dtype dt) {
   std::lock_guard<std::mutex> lk(g_table_mu);
-  return g_bs_table[class_of(n)];
+  return g_bs_table[table_index(dt)][class_of(n)];
 }
 
 constexpr size_t kAl = 256;
@@ -494,7 +499,7 @@ fw_status fw_batched_plan_create(fw_batched_plan** plan, const int64_t* n, const
   p->bs.resize(batch);
   p->R.resize(batch);
   for (int64_t g = 0; g < batch; ++g) {
-    p->bs[g] = o.bs ? o.bs : table_bs(n[g]);
+    p->bs[g] = o.bs ? o.bs : table_bs(n[g], dtype);
     p->R[g] = (int)((n[g] + p->bs[g] - 1) / p->bs[g]);
     if (p->R[g] > 1024) {
       delete p;
@@ -551,15 +556,18 @@ fw_status fw_batched_plan_destroy(fw_batched_plan* p) {
   return FW_OK;
 }
 
-fw_status fw_bs_table(int32_t* table, int32_t set) {
+fw_status fw_bs_table(fw_dtype dtype, int32_t* table, int32_t set) {
   if (!table) return FW_ERR_ARG;
+  if (dtype == FW_I64 || dtype == FW_F64) return FW_ERR_UNSUPPORTED;  // no batched path
+  if (dtype != FW_I32 && dtype != FW_F32) return FW_ERR_ARG;
   std::lock_guard<std::mutex> lk(g_table_mu);
+  int* t = g_bs_table[table_index(dtype)];
   if (set) {
     for (int c = 0; c < kClasses; ++c)
       if (table[c] != 32 && table[c] != 64 && table[c] != 128) return FW_ERR_ARG;
-    for (int c = 0; c < kClasses; ++c) g_bs_table[c] = table[c];
+    for (int c = 0; c < kClasses; ++c) t[c] = table[c];
   } else {
-    for (int c = 0; c < kClasses; ++c) table[c] = g_bs_table[c];
+    for (int c = 0; c < kClasses; ++c) table[c] = t[c];
   }
   return FW_OK;
 }
@@ -571,7 +579,7 @@ fw_status fw_autotune_bs(fw_dtype dtype, int64_t graphs_per_class, int64_t max_n
   if (graphs_per_class < 1 || graphs_per_class > 4096 || max_n < 1) return FW_ERR_ARG;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   int32_t table[kClasses];
-  fw_bs_table(table, 0);
+  fw_bs_table(dtype, table, 0);
   const int cand[3] = {32, 64, 128};
   for (int c = 0; c < kClasses; ++c) {
     const int64_t n = std::min<int64_t>(c + 1 < kClasses ? kClassMax[c] : 8192, max_n);
@@ -631,7 +639,7 @@ fw_status fw_autotune_bs(fw_dtype dtype, int64_t graphs_per_class, int64_t max_n
     table[c] = best;
     if (ms_out) ms_out[c] = best_ms;
   }
-  fw_bs_table(table, 1);
+  fw_bs_table(dtype, table, 1);
   if (table_out)
     for (int c = 0; c < kClasses; ++c) table_out[c] = table[c];
   return FW_OK;

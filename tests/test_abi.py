@@ -142,12 +142,23 @@ def test_batched_host_checks(fw):
 
 
 def test_bs_table_host(fw):
-    t = fw.fw_bs_table()
-    assert len(t) == 7 and set(t.tolist()) <= {32, 64, 128}
+    """One table per element type (the 64-bit types have no batched path);
+    writing one leaves the other alone."""
+    ti, tf = fw.fw_bs_table(), fw.fw_bs_table(dtype=fw.FW_F32)
+    for t in (ti, tf):
+        assert len(t) == 7 and set(t.tolist()) <= {32, 64, 128}
     with pytest.raises(fw.FWError):
         fw.fw_bs_table(np.array([32, 32, 48, 64, 128, 128, 128], np.int32))
-    fw.fw_bs_table(t)
-    assert (fw.fw_bs_table() == t).all()
+    for dt in (fw.FW_I64, fw.FW_F64, 7):
+        with pytest.raises(fw.FWError):
+            fw.fw_bs_table(dtype=dt)
+    other = np.array([32, 32, 32, 32, 32, 32, 32], np.int32)
+    fw.fw_bs_table(other, dtype=fw.FW_F32)
+    assert (fw.fw_bs_table(dtype=fw.FW_F32) == other).all()
+    assert (fw.fw_bs_table() == ti).all()
+    fw.fw_bs_table(tf, dtype=fw.FW_F32)
+    fw.fw_bs_table(ti)
+    assert (fw.fw_bs_table() == ti).all() and (fw.fw_bs_table(dtype=fw.FW_F32) == tf).all()
 
 
 def test_solve_plan_choices(fw):

@@ -105,13 +105,21 @@ def test_batched_config_shape_sampled():
 
 
 def test_bs_table_and_autotune():
+    """The autotuner fills the table of the element type it measured, for the
+    classes up to max_n, and leaves the other type's table alone."""
     m = fw()
-    old = m.fw_bs_table()
-    table, ms = m.fw_autotune_bs(m.FW_I32, graphs_per_class=6, max_n=300)
-    assert set(table.tolist()) <= {32, 64, 128}
-    assert (ms[:2] > 0).all()
-    assert (m.fw_bs_table() == table).all()
-    m.fw_bs_table(old)
+    old_i, old_f = m.fw_bs_table(), m.fw_bs_table(dtype=m.FW_F32)
+    try:
+        for dt, other in ((m.FW_I32, m.FW_F32), (m.FW_F32, m.FW_I32)):
+            before = m.fw_bs_table(dtype=other)
+            table, ms = m.fw_autotune_bs(dt, graphs_per_class=6, max_n=300)
+            assert set(table.tolist()) <= {32, 64, 128}
+            assert (ms[:3] > 0).all() and (ms[3:] == 0).all()
+            assert (m.fw_bs_table(dtype=dt) == table).all()
+            assert (m.fw_bs_table(dtype=other) == before).all()
+    finally:
+        m.fw_bs_table(old_i)
+        m.fw_bs_table(old_f, dtype=m.FW_F32)
 
 
 def test_batched_distance_only():
