@@ -12,6 +12,8 @@ its row and column, phase 4 on the rest; strict "<", first minimising k) twice
 on small integer graphs -- once storing last hops throughout, once with the via
 encoding and the final chain resolution -- and requires identical
 predecessor matrices.  Plain Python loops, no GPU; independent of the oracle.
+A second replay follows the persistent engine as it is now, whose panel tasks
+record via codes too (a chain then takes at most two links per round).
 """
 import numpy as np
 import pytest
