@@ -111,11 +111,15 @@ typedef struct fw_options {
                                  each, saturating), column 8 = cycles from task start to the end
                                  of the relaxation | whole task << 32.  Pivot and panel tasks:
                                  column 7 = operands loaded | relaxed << 32, column 8 = results
-                                 stored | whole task << 32 (SM cycles from the task's start) */
+                                 stored | whole task << 32 (SM cycles from the task's start).
+                                 Column 0 = task | type << 32 | graph << 40, type 0-3 as in
+                                 fw_queue_tasks and 4 for remaining tile (r+1, r+1) of round r
+                                 run together with the pivot of round r+1 (that pivot's own
+                                 entry is then skipped and not traced) */
   int64_t trace_cap;
   int32_t trace_stride;
-  int32_t tile_tma;           /* persistent driver: 1 (default) loads each remaining tile with one
-                                 2-D TMA tensor copy, 0 = one bulk copy per tile row */
+  int32_t tile_tma;           /* persistent driver: 1 (default) loads each remaining or panel
+                                 tile with one 2-D TMA tensor copy, 0 = one bulk copy per row */
 } fw_options;
 
 /* Fills *opt with the defaults used by fw_solve. */
