@@ -491,7 +491,7 @@ def trace_config(fw, name, out_path):
     D = torch.empty_like(W)
     P = torch.empty((n, ld), dtype=torch.int32, device="cuda")
     sms = torch.cuda.get_device_properties(0).multi_processor_count
-    plan = fw.fw_solve_plan(n, fw.Options.default(bs=bs), sms)
+    plan = fw.fw_solve_plan(n, fw.Options.default(bs=bs), sms, dtype=dt)
     R, look = plan["rounds"], plan["lookahead"]
     tr = torch.zeros((R ** 3, 10), dtype=torch.int64, device="cuda")
     opt = fw.Options.default(bs=bs, trace=tr.data_ptr(), trace_cap=R ** 3, trace_stride=1)

@@ -344,17 +344,20 @@ fw_status fw_intermediate(const int32_t* pred, int32_t* out, int64_t n, int64_t 
                           int64_t batch, int64_t stride, void* stream);
 
 /*
- * fw_solve_plan: what fw_solve_ex would choose for n vertices and *opt (NULL:
- * defaults) on a GPU with `sms` co-resident CTAs (one per SM): the block size
+ * fw_solve_plan: what fw_solve_ex would choose for n vertices of element type
+ * dtype and *opt (NULL: defaults) on a GPU with `sms` co-resident CTAs (one
+ * per SM): the block size
  * BS, the number of rounds R = ceil(n / BS) (Sec. 2.3), the lookahead of the
  * persistent queue, and the bytes of device workspace it keeps per (device,
  * stream) besides the caller's matrices (tile versions, queue offsets, pivot
  * and panel snapshots).  Any output pointer may be NULL.  Host only: no CUDA
- * call.  FW_ERR_ARG for n outside [1, 131072], sms < 1 or invalid options;
- * FW_ERR_UNSUPPORTED when R would exceed 1024.
+ * call.  FW_ERR_ARG for n outside [1, 131072], sms < 1, an invalid dtype or
+ * invalid options; FW_ERR_UNSUPPORTED when R would exceed 1024 or a 64-bit
+ * dtype is given BS = 128 (as fw_solve_ex).
  */
-fw_status fw_solve_plan(int64_t n, const fw_options* opt, int32_t sms, int32_t* bs,
-                        int32_t* rounds, int64_t* lookahead, int64_t* workspace_bytes);
+fw_status fw_solve_plan(int64_t n, fw_dtype dtype, const fw_options* opt, int32_t sms,
+                        int32_t* bs, int32_t* rounds, int64_t* lookahead,
+                        int64_t* workspace_bytes);
 
 /*
  * fw_queue_tasks: diagnostic view of the persistent driver's task queue for R

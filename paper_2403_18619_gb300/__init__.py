@@ -104,7 +104,7 @@ def load():
         lib.fw_peak_probe.argtypes = [I32, P, P, P, P]
         lib.fw_verify_certificate.argtypes = [P, P, P, I64, I64, P, P]
         lib.fw_queue_tasks.argtypes = [I32, I64, I64, I64, P]
-        lib.fw_solve_plan.argtypes = [I64, P, I32, P, P, P, P]
+        lib.fw_solve_plan.argtypes = [I64, I32, P, I32, P, P, P, P]
         lib.fw_paths.argtypes = [P, I64, I64, P, P, I64, P, I64, P, P]
         lib.fw_intermediate.argtypes = [P, P, I64, I64, I64, I64, P]
         lib.fw_solve_noalloc.argtypes = [P, P, I64, I64, I32, P]
@@ -320,13 +320,15 @@ def fw_intermediate(pred, out=None, stream=None):
     return out
 
 
-def fw_solve_plan(n: int, options: Options | None = None, sms: int = 152) -> dict:
-    """What fw_solve_ex would choose for n vertices on a GPU with `sms` SMs:
-    block size, rounds, queue lookahead and device workspace bytes (host only)."""
+def fw_solve_plan(n: int, options: Options | None = None, sms: int = 152,
+                  dtype: int = FW_I32) -> dict:
+    """What fw_solve_ex would choose for n vertices of `dtype` on a GPU with
+    `sms` SMs: block size, rounds, queue lookahead and device workspace bytes
+    (host only)."""
     bs, rounds = ctypes.c_int32(), ctypes.c_int32()
     look, ws = ctypes.c_int64(), ctypes.c_int64()
     o = ctypes.byref(options) if options is not None else None
-    check(load().fw_solve_plan(n, o, sms, ctypes.byref(bs), ctypes.byref(rounds),
+    check(load().fw_solve_plan(n, dtype, o, sms, ctypes.byref(bs), ctypes.byref(rounds),
                                ctypes.byref(look), ctypes.byref(ws)), "fw_solve_plan")
     return {"bs": bs.value, "rounds": rounds.value, "lookahead": look.value,
             "workspace_bytes": ws.value}

@@ -476,21 +476,24 @@ fw_status fw_release_workspace(void) {
   return FW_OK;
 }
 
-fw_status fw_solve_plan(int64_t n, const fw_options* opt, int32_t sms, int32_t* bs,
-                        int32_t* rounds, int64_t* lookahead, int64_t* workspace_bytes) {
+fw_status fw_solve_plan(int64_t n, fw_dtype dtype, const fw_options* opt, int32_t sms,
+                        int32_t* bs, int32_t* rounds, int64_t* lookahead,
+                        int64_t* workspace_bytes) {
   fw_options o;
   if (opt) o = *opt;
   else fw_options_default(&o);
-  if (n <= 0 || n > 131072 || sms < 1) return FW_ERR_ARG;
+  if (n <= 0 || n > 131072 || sms < 1 || !dtype_valid(dtype)) return FW_ERR_ARG;
   if (check_options(o) != FW_OK) return FW_ERR_ARG;
-  const int BS = o.bs ? o.bs : pick_bs(n);
+  const bool wide = dtype_size(dtype) == 8;
+  if (wide && o.bs == 128) return FW_ERR_UNSUPPORTED;  // 64-bit types take BS 32 or 64
+  const int BS = o.bs ? o.bs : pick_bs(n, dtype);
   const int64_t R64 = (n + BS - 1) / BS;
   if (R64 > 1024) return FW_ERR_UNSUPPORTED;
   const int R = (int)R64;
   if (bs) *bs = BS;
   if (rounds) *rounds = R;
   if (lookahead) *lookahead = o.lookahead < 0 ? auto_lookahead(R, sms) : o.lookahead;
-  if (workspace_bytes) *workspace_bytes = (int64_t)solve_ws_bytes(R, BS);
+  if (workspace_bytes) *workspace_bytes = (int64_t)solve_ws_bytes(R, BS, dtype_size(dtype));
   return FW_OK;
 }
 

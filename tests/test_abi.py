@@ -176,10 +176,23 @@ def test_solve_plan_choices(fw):
     p = fw.fw_solve_plan(1024, fw.Options.default(bs=128), sms=152)
     assert p["lookahead"] == 2 * 152
     assert fw.fw_solve_plan(8192, fw.Options.default(lookahead=77))["lookahead"] == 77
+    # 64-bit elements: BS 64 above 512 vertices, no BS = 128, snapshots of 8-byte
+    # elements without the packed keys
+    for dt in (fw.FW_I64, fw.FW_F64):
+        p8 = fw.fw_solve_plan(8192, sms=152, dtype=dt)
+        assert p8["bs"] == 64 and p8["rounds"] == 128
+        assert fw.fw_solve_plan(300, dtype=dt)["bs"] == 32
+        with pytest.raises(fw.FWError) as e:
+            fw.fw_solve_plan(8192, fw.Options.default(bs=128), dtype=dt)
+        assert e.value.code == 6
+    p4 = fw.fw_solve_plan(8192, fw.Options.default(bs=64), sms=152)
+    p8 = fw.fw_solve_plan(8192, fw.Options.default(bs=64), sms=152, dtype=fw.FW_F64)
+    assert p8["workspace_bytes"] != p4["workspace_bytes"]
     lib = fw.load()
-    assert lib.fw_solve_plan(0, None, 152, None, None, None, None) == 1
-    assert lib.fw_solve_plan(100, None, 0, None, None, None, None) == 1
-    assert lib.fw_solve_plan(131072, ctypes.byref(fw.Options.default(bs=32)), 152,
+    assert lib.fw_solve_plan(0, fw.FW_I32, None, 152, None, None, None, None) == 1
+    assert lib.fw_solve_plan(100, fw.FW_I32, None, 0, None, None, None, None) == 1
+    assert lib.fw_solve_plan(100, 9, None, 152, None, None, None, None) == 1
+    assert lib.fw_solve_plan(131072, fw.FW_I32, ctypes.byref(fw.Options.default(bs=32)), 152,
                              None, None, None, None) == 6
 
 
