@@ -150,7 +150,8 @@ fw_status fw_solve_ex(void* dist, int32_t* pred, int64_t n, int64_t ld, fw_dtype
 /*
  * fw_solve_host: the same solve on HOST buffers.  dist_host (n x ld, dtype)
  * is copied to the device, solved, and dist_host / pred_host (n x ld int32)
- * receive the results (pred_host NULL: distances only).  Pinned host memory
+ * receive the results (pred_host NULL: distances only); the columns n..ld-1
+ * of the host buffers are neither read nor written.  Pinned host memory
  * gives full copy bandwidth; pageable
  * memory works too.  Synchronous: returns after the results are on the host,
  * with any device-side error (as fw_sync_status would report it).  Device
@@ -161,6 +162,20 @@ fw_status fw_solve_ex(void* dist, int32_t* pred, int64_t n, int64_t ld, fw_dtype
  */
 fw_status fw_solve_host(void* dist_host, int32_t* pred_host, int64_t n, int64_t ld,
                         fw_dtype dtype, const fw_options* opt, void* stream);
+
+/*
+ * fw_solve_host_io: fw_solve_host with the weights in their own host buffer:
+ * w_host (n x ld, dtype) is copied to the device and left unchanged, and the
+ * distances go to dist_host (n x ld, dtype), the predecessors to pred_host
+ * (NULL: distances only).  dist_host == w_host is the in-place fw_solve_host;
+ * any other overlap of the buffers is not allowed.  A caller that solves
+ * the same or new weights again needs no copy of them to restore the input,
+ * and the results land in buffers that the host has not just rewritten
+ * (copies into host memory the CPU has just written ran up to 5x slower on
+ * GB300).  FW_ERR_ARG for a null w_host or dist_host, and as fw_solve_host.
+ */
+fw_status fw_solve_host_io(const void* w_host, void* dist_host, int32_t* pred_host, int64_t n,
+                           int64_t ld, fw_dtype dtype, const fw_options* opt, void* stream);
 
 /*
  * Batched solve of many independent graphs of different sizes in one

@@ -16,7 +16,7 @@ import numpy as np
 
 __all__ = [
     "FWError", "Options", "load", "check", "fw_solve", "fw_solve_ex", "fw_solve_host",
-    "fw_solve_noalloc", "fw_sync_status", "fw_backward", "fw_backward_strided",
+    "fw_solve_host_io", "fw_solve_noalloc", "fw_sync_status", "fw_backward", "fw_backward_strided",
     "fw_peak_probe", "fw_verify_certificate", "fw_release_workspace", "fw_solve_plan",
     "fw_queue_tasks", "fw_paths", "fw_intermediate", "fw_tile_closure", "fw_tile_minplus", "fw_block_init_pred",
     "BatchedPlan", "fw_bs_table", "fw_autotune_bs", "padded", "solve",
@@ -93,6 +93,7 @@ def load():
         lib.fw_solve.argtypes = [P, P, I64, I64, I32, P]
         lib.fw_solve_ex.argtypes = [P, P, I64, I64, I32, P, P]
         lib.fw_solve_host.argtypes = [P, P, I64, I64, I32, P, P]
+        lib.fw_solve_host_io.argtypes = [P, P, P, I64, I64, I32, P, P]
         lib.fw_batched_plan_create.argtypes = [P, P, P, I64, I32, P]
         lib.fw_solve_batched.argtypes = [P, P, P, P]
         lib.fw_batched_plan_info.argtypes = [P, P, P]
@@ -115,7 +116,8 @@ def load():
                                            I32, P]
         lib.fw_bs_table.argtypes = [I32, P, I32]
         lib.fw_autotune_bs.argtypes = [I32, I64, I64, P, P, P]
-        for name in ("fw_solve", "fw_solve_ex", "fw_solve_host", "fw_batched_plan_create",
+        for name in ("fw_solve", "fw_solve_ex", "fw_solve_host", "fw_solve_host_io",
+                     "fw_batched_plan_create",
                      "fw_solve_batched", "fw_batched_plan_info", "fw_batched_plan_destroy",
                      "fw_backward", "fw_backward_strided", "fw_sync_status",
                      "fw_release_workspace", "fw_peak_probe", "fw_verify_certificate",
@@ -199,26 +201,54 @@ def fw_solve_noalloc(dist, pred, stream=None) -> None:
           "fw_solve_noalloc")
 
 
-def fw_solve_host(dist: np.ndarray, pred: np.ndarray, options: Options | None = None,
-                  stream=None) -> None:
-    """fw_solve_host on host arrays (numpy or pinned CPU torch tensors), synchronous."""
+def _host_matrix(a, name):
+    """(pointer, n, ld, dtype code) of a host matrix (numpy array or CPU torch
+    tensor) with unit column stride."""
     import torch
-    if isinstance(dist, torch.Tensor):
-        dptr, n, ld = dist.data_ptr(), dist.shape[0], dist.stride(0)
-        code = _dtype_code(dist)
-        pptr = pred.data_ptr() if pred is not None else None
-    else:
-        if dist.ndim != 2 or dist.strides[1] != dist.itemsize:
-            raise ValueError("dist must be a 2-D array with unit column stride")
-        n, ld = dist.shape[0], dist.strides[0] // dist.itemsize
-        code = {np.dtype(np.int32): FW_I32, np.dtype(np.float32): FW_F32,
-                np.dtype(np.int64): FW_I64, np.dtype(np.float64): FW_F64}.get(dist.dtype)
-        if code is None:
-            raise TypeError("dist must be int32, float32, int64 or float64")
-        dptr = dist.ctypes.data
-        pptr = pred.ctypes.data if pred is not None else None
+    if isinstance(a, torch.Tensor):
+        if a.is_cuda or a.dim() != 2 or a.stride(1) != 1 or a.shape[0] != a.shape[1]:
+            raise ValueError("%s must be an n x n host view with unit column stride" % name)
+        return a.data_ptr(), a.shape[0], a.stride(0), _dtype_code(a)
+    if a.ndim != 2 or a.strides[1] != a.itemsize or a.shape[0] != a.shape[1]:
+        raise ValueError("%s must be an n x n array with unit column stride" % name)
+    code = {np.dtype(np.int32): FW_I32, np.dtype(np.float32): FW_F32,
+            np.dtype(np.int64): FW_I64, np.dtype(np.float64): FW_F64}.get(a.dtype)
+    if code is None:
+        raise TypeError("%s must be int32, float32, int64 or float64" % name)
+    return a.ctypes.data, a.shape[0], a.strides[0] // a.itemsize, code
+
+
+def _host_pred(pred, n, ld):
+    """Pointer of a host int32 predecessor matrix (n x n, row stride ld), or
+    None for a distance-only solve."""
+    if pred is None:
+        return None
+    pp, pn, pld, pcode = _host_matrix(pred, "pred")
+    if (pn, pld, pcode) != (n, ld, FW_I32):
+        raise ValueError("pred must be int32 with the distances' shape and row stride")
+    return pp
+
+
+def fw_solve_host(dist, pred, options: Options | None = None, stream=None) -> None:
+    """fw_solve_host on host arrays (numpy or pinned CPU torch tensors), synchronous:
+    dist holds the weights on entry and the distances on exit."""
+    dptr, n, ld, code = _host_matrix(dist, "dist")
     o = ctypes.byref(options) if options is not None else None
-    check(load().fw_solve_host(dptr, pptr, n, ld, code, o, _stream_ptr(stream)), "fw_solve_host")
+    check(load().fw_solve_host(dptr, _host_pred(pred, n, ld), n, ld, code, o,
+                               _stream_ptr(stream)), "fw_solve_host")
+
+
+def fw_solve_host_io(weights, dist, pred, options: Options | None = None, stream=None) -> None:
+    """fw_solve_host_io: weights (host, left unchanged) in, distances and
+    predecessors out to their own host buffers (same shape and row stride);
+    synchronous."""
+    wptr, n, ld, code = _host_matrix(weights, "weights")
+    dptr, n2, ld2, code2 = _host_matrix(dist, "dist")
+    if (n2, ld2, code2) != (n, ld, code):
+        raise ValueError("dist must have the weights' shape, row stride and dtype")
+    o = ctypes.byref(options) if options is not None else None
+    check(load().fw_solve_host_io(wptr, dptr, _host_pred(pred, n, ld), n, ld, code, o,
+                                  _stream_ptr(stream)), "fw_solve_host_io")
 
 
 def fw_backward(grad_dist, dist, pred, grad_w, stream=None) -> None:

@@ -391,12 +391,16 @@ fw_status fw_sync_status(void* stream) {
 
 fw_status fw_solve_host(void* dist_host, int32_t* pred_host, int64_t n, int64_t ld,
                         fw_dtype dtype, const fw_options* opt, void* stream) {
-  if (!dist_host) return FW_ERR_ARG;
+  return fw_solve_host_io(dist_host, dist_host, pred_host, n, ld, dtype, opt, stream);
+}
+
+fw_status fw_solve_host_io(const void* w_host, void* dist_host, int32_t* pred_host, int64_t n,
+                           int64_t ld, fw_dtype dtype, const fw_options* opt, void* stream) {
+  if (!w_host || !dist_host) return FW_ERR_ARG;
   if (n <= 0 || n > 131072 || ld < n || (ld % 4) != 0) return FW_ERR_ARG;
   if (!dtype_valid(dtype)) return FW_ERR_ARG;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  const size_t bytes = (size_t)n * ld * dtype_size(dtype);  // dist
-  const size_t pbytes = (size_t)n * ld * 4;                 // pred
+  const size_t bytes = (size_t)n * ld * dtype_size(dtype);  // dist (pred needs no more)
   void* dd = nullptr;
   void* dp = nullptr;
   cudaStream_t side = nullptr;
@@ -434,7 +438,12 @@ fw_status fw_solve_host(void* dist_host, int32_t* pred_host, int64_t n, int64_t 
     ev_side = w.ev_side;
     o.ev_stop = o.ev_stop ? o.ev_stop : reinterpret_cast<void*>(w.ev_solved);
   }
-  if (cudaMemcpyAsync(dd, dist_host, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
+  // the n x n block only (rows ld apart): the caller's padding columns are
+  // neither read nor written
+  const size_t pitch = (size_t)ld * dtype_size(dtype), width = (size_t)n * dtype_size(dtype);
+  const size_t ppitch = (size_t)ld * 4, pwidth = (size_t)n * 4;
+  if (cudaMemcpy2DAsync(dd, pitch, w_host, pitch, width, (size_t)n, cudaMemcpyHostToDevice, s) !=
+      cudaSuccess)
     return FW_ERR_CUDA;
   fw_status st = fw_solve_ex(dd, pred_host ? reinterpret_cast<int32_t*>(dp) : nullptr, n, ld,
                              dtype, &o, stream);
@@ -442,10 +451,11 @@ fw_status fw_solve_host(void* dist_host, int32_t* pred_host, int64_t n, int64_t 
   // The distances are final at ev_stop (the int32 solve's last pass rewrites
   // only pred): they leave on the side stream while that pass runs.
   if (cudaStreamWaitEvent(side, reinterpret_cast<cudaEvent_t>(o.ev_stop), 0) != cudaSuccess ||
-      cudaMemcpyAsync(dist_host, dd, bytes, cudaMemcpyDeviceToHost, side) != cudaSuccess ||
+      cudaMemcpy2DAsync(dist_host, pitch, dd, pitch, width, (size_t)n, cudaMemcpyDeviceToHost,
+                        side) != cudaSuccess ||
       cudaEventRecord(ev_side, side) != cudaSuccess ||
-      (pred_host &&
-       cudaMemcpyAsync(pred_host, dp, pbytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) ||
+      (pred_host && cudaMemcpy2DAsync(pred_host, ppitch, dp, ppitch, pwidth, (size_t)n,
+                                      cudaMemcpyDeviceToHost, s) != cudaSuccess) ||
       cudaStreamWaitEvent(s, ev_side, 0) != cudaSuccess)
     return FW_ERR_CUDA;
   return fw_sync_status(stream);

@@ -209,6 +209,19 @@ def test_paths_argument_checks(fw):
     assert lib.fw_paths(p, 10, 10, p, p, 0, p, 4, p, None) == 0
 
 
+def test_host_io_argument_checks(fw):
+    """fw_solve_host_io's host checks: null weights or distance buffers, and
+    the in-place entry point's own checks (no CUDA call is reached)."""
+    lib = fw.load()
+    p = ctypes.c_void_p(16)
+    assert lib.fw_solve_host_io(None, p, None, 10, 12, fw.FW_I32, None, None) == 1
+    assert lib.fw_solve_host_io(p, None, None, 10, 12, fw.FW_I32, None, None) == 1
+    assert lib.fw_solve_host_io(p, p, None, 0, 12, fw.FW_I32, None, None) == 1
+    assert lib.fw_solve_host_io(p, p, None, 10, 10, fw.FW_I32, None, None) == 1   # ld % 4
+    assert lib.fw_solve_host_io(p, p, None, 10, 12, 9, None, None) == 1
+    assert lib.fw_solve_host(None, None, 10, 12, fw.FW_I32, None, None) == 1
+
+
 def test_intermediate_argument_checks(fw):
     """fw_intermediate's host checks (no launch; batch 0 is a no-op)."""
     lib = fw.load()

@@ -221,6 +221,42 @@ def test_host_buffer_path_events_and_repeats(dtype):
         assert e0.elapsed_time(e1) > 0
 
 
+@pytest.mark.parametrize("dtype", ["i32", "f64"])
+def test_host_io_out_of_place(dtype):
+    """fw_solve_host_io: the weights' host buffer is left unchanged, the
+    results land in their own buffers (pinned tensors here, padded rows), and
+    in place (dist is the weights' buffer) it is fw_solve_host."""
+    import torch
+    m = fw()
+    n, ld = 301, 308
+    if dtype == "i32":
+        W, Do, Po, cnt = int_case(n, 9, 0.4, 1, 70)
+    else:
+        W = graphgen.dense_graph_f64(n, seed=9, p=0.4)
+        Do, Po = oracle.fw_f64(W)
+    tdt = torch.int32 if dtype == "i32" else torch.float64
+    Wb = torch.zeros((n, ld), dtype=tdt, pin_memory=True)
+    Wb[:, :n] = torch.from_numpy(W)
+    Db = torch.full((n, ld), 5, dtype=tdt).pin_memory()
+    Pb = torch.full((n, ld), 7, dtype=torch.int32).pin_memory()
+    keep = Wb.clone()
+    for _ in range(2):
+        m.fw_solve_host_io(Wb[:, :n], Db[:, :n], Pb[:, :n])
+        assert torch.equal(Wb, keep)                       # weights untouched, padding too
+        assert (Db[:, n:] == 5).all() and (Pb[:, n:] == 7).all()
+        D, P = Db[:, :n].numpy(), Pb[:, :n].numpy()
+        if dtype == "i32":
+            check_int_full(W, D, P, Do, Po, cnt)
+        else:
+            from test_gpu_wide import _check_f64
+            _check_f64(W, D, P, Do, Po)
+    # in place through the same entry point
+    m.fw_solve_host_io(Wb[:, :n], Wb[:, :n], None)
+    np.testing.assert_array_equal(Wb[:, :n].numpy(), Db[:, :n].numpy())
+    with pytest.raises(ValueError):
+        m.fw_solve_host_io(Wb[:, :n], Db[:, :n - 1], None)
+
+
 # ------------------------------------------------------------------- fp32 ---
 
 @pytest.mark.parametrize("driver", [PERSISTENT, PHASED])
