@@ -814,10 +814,13 @@ __device__ __forceinline__ bool wait_ge(const int* p, int target, int* abort_fla
   const uint64_t t0 = globaltimer();
   // iteration cap as well as the clock: each iteration sleeps >= 32 ns
   const int64_t max_it = timeout_ns / 32 + 1024;
+  // sleeps back off to 64 ns at most: a flag is polled soon after it is
+  // published (n = 1024 at BS = 32: 0.610 -> 0.606 ms against 256 ns; the
+  // large solves and the batched workload unchanged)
   unsigned ns = 32;
   for (int64_t it = 0;; ++it) {
     __nanosleep(ns);
-    if (ns < 256) ns <<= 1;
+    if (ns < 64) ns <<= 1;
     if (ld_acquire(p) >= target) return true;
     if (ld_relaxed(abort_flag)) return false;
     if (globaltimer() - t0 > (uint64_t)timeout_ns || it > max_it) {
