@@ -5,14 +5,17 @@
 // A CTA has 8 compute warps, 1 producer warp and 1 publisher warp.
 //   * The producer claims tasks from a global queue in order, waits (bounded)
 //     on the tiles' ready flags, and streams the operands of remaining-tile
-//     tasks into shared memory with TMA bulk copies while the compute warps
-//     work on the previous task:
-//       - the tile's own D block (one bulk copy per row)          -> Dbuf
+//     tasks into shared memory with TMA copies while the compute warps work
+//     on the previous task:
+//       - the tile's own D block (one 2-D tensor copy, or one copy per row) -> Dbuf
 //       - the A and B panel snapshots, 64 (fp32: 32) k-steps per chunk -> 2-stage ring
-//       - the predecessor tile of the B panel (for the epilogue)  -> Pbuf
+//       - the predecessor tile of the B panel (fp32 epilogue)          -> Pbuf
+//     and, for int32 panel tasks, the tile and the closed pivot (ws_panel).
 //   * The compute warps relax (min-plus over the chunks) and store improved
-//     entries; pivot and panel tasks are run by them alone, using the shared
-//     buffer as scratch (the producer waits until such a task is published).
+//     entries; pivot tasks (and the panels of the other element types) are
+//     run by them alone, using the shared buffer as scratch (the producer
+//     waits until such a task is published).  The task that finishes tile
+//     (r+1, r+1) of round r runs the pivot of round r+1 right after it.
 //   * The publisher sleeps on the compute warps' task-done barrier and
 //     publishes each finished tile (the GPU-scope release), so that neither the
 //     compute warps nor the producer wait on that fence.
