@@ -439,11 +439,15 @@ fw_status fw_solve_host_io(const void* w_host, void* dist_host, int32_t* pred_ho
     o.ev_stop = o.ev_stop ? o.ev_stop : reinterpret_cast<void*>(w.ev_solved);
   }
   // the n x n block only (rows ld apart): the caller's padding columns are
-  // neither read nor written
+  // neither read nor written (one plain copy when there are none)
   const size_t pitch = (size_t)ld * dtype_size(dtype), width = (size_t)n * dtype_size(dtype);
   const size_t ppitch = (size_t)ld * 4, pwidth = (size_t)n * 4;
-  if (cudaMemcpy2DAsync(dd, pitch, w_host, pitch, width, (size_t)n, cudaMemcpyHostToDevice, s) !=
-      cudaSuccess)
+  auto copy_block = [&](void* dst, const void* src, size_t p, size_t w, cudaMemcpyKind kind,
+                        cudaStream_t st) {
+    return p == w ? cudaMemcpyAsync(dst, src, w * (size_t)n, kind, st)
+                  : cudaMemcpy2DAsync(dst, p, src, p, w, (size_t)n, kind, st);
+  };
+  if (copy_block(dd, w_host, pitch, width, cudaMemcpyHostToDevice, s) != cudaSuccess)
     return FW_ERR_CUDA;
   fw_status st = fw_solve_ex(dd, pred_host ? reinterpret_cast<int32_t*>(dp) : nullptr, n, ld,
                              dtype, &o, stream);
@@ -451,11 +455,10 @@ fw_status fw_solve_host_io(const void* w_host, void* dist_host, int32_t* pred_ho
   // The distances are final at ev_stop (the int32 solve's last pass rewrites
   // only pred): they leave on the side stream while that pass runs.
   if (cudaStreamWaitEvent(side, reinterpret_cast<cudaEvent_t>(o.ev_stop), 0) != cudaSuccess ||
-      cudaMemcpy2DAsync(dist_host, pitch, dd, pitch, width, (size_t)n, cudaMemcpyDeviceToHost,
-                        side) != cudaSuccess ||
+      copy_block(dist_host, dd, pitch, width, cudaMemcpyDeviceToHost, side) != cudaSuccess ||
       cudaEventRecord(ev_side, side) != cudaSuccess ||
-      (pred_host && cudaMemcpy2DAsync(pred_host, ppitch, dp, ppitch, pwidth, (size_t)n,
-                                      cudaMemcpyDeviceToHost, s) != cudaSuccess) ||
+      (pred_host &&
+       copy_block(pred_host, dp, ppitch, pwidth, cudaMemcpyDeviceToHost, s) != cudaSuccess) ||
       cudaStreamWaitEvent(s, ev_side, 0) != cudaSuccess)
     return FW_ERR_CUDA;
   return fw_sync_status(stream);
