@@ -595,18 +595,78 @@ __device__ __forceinline__ void core_packed(const uint32_t* __restrict__ As,
   }
 }
 
+// 1.0f when a < b, else 0.0f, in one instruction (PTX set with a float
+// destination).
+__device__ __forceinline__ float lt_one(float a, float b) {
+  float r;
+  asm("set.lt.f32.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+  return r;
+}
+
+// fp32 argmin accumulator -> step + 1 (0: no improvement).  The accumulator
+// (arg's bits, see core_generic) is 0 or lies in [2^k, 2^(k+1)) for the last
+// improving step k, so its exponent field is k + 127.
+template <typename T, int TM>
+__device__ __forceinline__ void argmin_finish(int (&arg)[TM][TM]) {
+  if constexpr (std::is_same<T, float>::value) {
+#pragma unroll
+    for (int m = 0; m < TM; ++m)
+#pragma unroll
+      for (int nn = 0; nn < TM; ++nn) arg[m][nn] = arg[m][nn] ? (arg[m][nn] >> 23) - 126 : 0;
+  }
+}
+
 // Generic relaxation with an explicit first-argmin: s = A + B; if (s < acc)
-// { acc = s; arg = kk + 1 }.  Used for fp32 and for int32 tiles whose values
-// exceed the packed-key bound.
-template <int BS, typename T, int K = BS>
+// { acc = s; arg = kk + 1 }.  Used for fp32, the 64-bit types and int32
+// tiles whose values exceed the packed-key bound.
+//
+// fp32 keeps the argmin on the FMA pipe: while the steps run, arg holds the
+// bits of a float accumulator to which every improving step k = kk0 + kk adds
+// 2^k, rounded toward zero.  Toward zero, a sum of distinct powers of two
+// never reaches the power of two above its largest term, so the
+// accumulator's exponent is the last improving step -- the first step that
+// reached the final minimum, as with the strict compare.  Per relaxation:
+// add, set (1.0 / 0.0), min and fma.rz, two ALU-pipe instructions where the
+// compare and two selects take three.  k < 128 keeps 2^k finite.  The
+// accumulator becomes step + 1 in argmin_finish, at the end of the call
+// (kFinish) or after a caller's last chunk.
+template <int BS, typename T, int K = BS, bool kFinish = true>
 __device__ __forceinline__ void core_generic(const T* __restrict__ As, const T* __restrict__ Bs,
                                              T (&acc)[Geo<BS>::TM][Geo<BS>::TM],
                                              int (&arg)[Geo<BS>::TM][Geo<BS>::TM], int tx, int ty,
                                              int kk0 = 0) {
   using Gm = Geo<BS>;
   constexpr int G = Gm::G, TM = Gm::TM;
-  // 2 steps (n = 8192 fp32 with predecessors 105.6 -> 102.8 ms, int64 252 -> 246 ms;
-  // 4 and 8 spill at the 168-register cap of the persistent kernel)
+  static_assert(BS <= 128, "the fp32 argmin accumulator holds steps below 128");
+  if constexpr (std::is_same<T, float>::value) {
+    // 2 steps (n = 8192 with predecessors: 98.4 ms, 99.8 with 1)
+#pragma unroll 2
+    for (int kk = 0; kk < K; ++kk) {
+      float a[TM], b[TM];
+#pragma unroll
+      for (int g = 0; g < Gm::NG; ++g) {
+        float ta[G], tb[G];
+        vload_s<G>(ta, As + kk * BS + g * Gm::SPAN + ty * G);
+        vload_s<G>(tb, Bs + kk * BS + g * Gm::SPAN + tx * G);
+#pragma unroll
+        for (int e = 0; e < G; ++e) { a[g * G + e] = ta[e]; b[g * G + e] = tb[e]; }
+      }
+      const float w = __int_as_float((127 + kk0 + kk) << 23);   // 2^(kk0 + kk)
+#pragma unroll
+      for (int m = 0; m < TM; ++m)
+#pragma unroll
+        for (int nn = 0; nn < TM; ++nn) {
+          const float s = a[m] + b[nn];
+          const float p = lt_one(s, acc[m][nn]);
+          acc[m][nn] = fminf(acc[m][nn], s);
+          arg[m][nn] = __float_as_int(__fmaf_rz(p, w, __int_as_float(arg[m][nn])));
+        }
+    }
+    if constexpr (kFinish) argmin_finish<T>(arg);
+    return;
+  }
+  // 2 steps (n = 8192 int64 252 -> 246 ms, and fp32 105.6 -> 102.8 ms when it
+  // took this loop; 4 and 8 spill at the 168-register cap of the persistent kernel)
 #pragma unroll 2
   for (int kk = 0; kk < K; ++kk) {
     T a[TM], b[TM];

@@ -424,11 +424,12 @@ __device__ __forceinline__ bool ws_minplus(TileCtx<T> c, int ti, int tj, bool fa
       decode_chunk<T, BS, C::CK>(ring + st * L::kStage, dec);
       const T* As = reinterpret_cast<const T*>(ring + st * L::kStage);
       const T* Bs = As + C::CK * BS;
-      core_generic<BS, T, C::CK>(As, Bs, old, arg, tx, ty, ch * C::CK);
+      core_generic<BS, T, C::CK, false>(As, Bs, old, arg, tx, ty, ch * C::CK);
       __syncwarp();
       if (lane == 0) mbar_arrive(&wb->chunk_empty[st]);
       ++pc.chunk;
     }
+    argmin_finish<T>(arg);
     const long long t_c = tr ? clock64() : 0;
     if constexpr (!ViaPred<T>::kOn) {
       // (this branch always has predecessors)
