@@ -1387,8 +1387,9 @@ __device__ __noinline__ int panel_packed(const Args<T>& a, int r, int t,
   return nb;
 }
 
-// Relaxation and epilogue of a panel tile with compare and select (fp32, or
-// int32 entries beyond the packed-key bound); operands raw in shared memory.
+// Relaxation and epilogue of a panel tile with an explicit argmin
+// (core_generic: fp32, or int32 entries beyond the packed-key bound);
+// operands raw in shared memory.
 template <typename T, int BS, bool is_row>
 __device__ __noinline__ int panel_eager(const Args<T>& a, int r, int t, const T* As,
                                         const T* Bs, const int32_t* Ps) {
