@@ -302,6 +302,37 @@ def test_f32_integer_weights_exact(n, bs):
         len(bad), bad[0].tolist(), P[tuple(bad[0])], P2[tuple(bad[0])])
 
 
+@pytest.mark.parametrize("driver", [PERSISTENT, PHASED])
+def test_f32_argmin_every_step_improves(driver):
+    """Entries that improve at every step of a 128-step block, in a row panel
+    and in a remaining tile.  Vertex 0 reaches each k = 1..127 of block 0 at
+    1000 - k, each of those k reaches every target 384..511 at 1, and the
+    sources 256..383 reach each k of block 0 at 2000 - k.  In round 0 the row
+    panel entry (0, j) improves at steps 1..127 (to 874) and the remaining
+    tile entry (i, j) at every step 0..127 (2874 through vertex 0, then 2000 -
+    k + 1): the strict minimum is the last step, k = 127.  This is the
+    extreme case of the fp32 argmin accumulator (2^0 + ... + 2^127, which must
+    stay below 2^128).  Distances and predecessors equal the int64 oracle's on
+    every entry (all weights are integers, so every fp32 sum is exact)."""
+    n, inf = 512, INF
+    W = np.full((n, n), inf, np.int32)
+    np.fill_diagonal(W, 0)
+    k = np.arange(128)
+    W[0, 1:128] = 1000 - k[1:]
+    W[np.ix_(np.arange(256, 384), k)] = (2000 - k)[None, :]
+    W[np.ix_(k[1:], np.arange(384, 512))] = 1
+    Do, Po = oracle.fw_i64(W)
+    cnt = oracle.path_count_i64(W, Do)
+    assert Do[300, 400] == 1874 and Po[300, 400] == 127
+    assert Do[0, 400] == 874 and Po[0, 400] == 127
+    Wf = np.where(W >= inf, np.inf, W).astype(np.float32)
+    D, P = gpu_solve(Wf, bs=128, driver=driver)
+    reach = np.isfinite(D)
+    assert (reach == (Do < inf)).all(), "reachability differs"
+    check_int_full(W, np.where(reach, D, inf).astype(np.int32), P, Do, Po, cnt)
+    assert (P[256:384, 384:] == 127).all() and (P[0, 384:] == 127).all()
+
+
 # ---------------------------------------------------------- error paths ---
 
 def test_negative_cycle_reported():
