@@ -77,45 +77,87 @@ __device__ __forceinline__ unsigned mid_word(unsigned anc, unsigned top1) { retu
 __device__ __forceinline__ unsigned mid_anc(unsigned w) { return w & 0xffffu; }
 __device__ __forceinline__ unsigned mid_top1(unsigned w) { return w >> 16; }  // largest + 1, 0: none
 
+// Word of vertex v from its last hop p (row i): ancestor p, nothing strictly
+// between them yet; no ancestor for the source, unreachable vertices and
+// entries outside [0, n).
+__device__ __forceinline__ unsigned mid_init(int v, int p, int i, int nn) {
+  const bool tree = v != i && p >= 0 && p < nn && p != v;
+  return mid_word(tree ? (unsigned)p : kNone, 0u);
+}
+// Result of a converged word: the largest intermediate vertex, -1 for none
+// (the edge itself) and for vertices whose walk never reached the source.
+__device__ __forceinline__ int32_t mid_out(unsigned w, int i) {
+  return mid_anc(w) == (unsigned)i ? (int32_t)mid_top1(w) - 1 : -1;
+}
+
+// One CTA per row.  vec: the row starts on a 16-byte boundary in both
+// matrices, so the row moves in 16-byte accesses (the n % 4 tail one by one),
+// several in flight per thread.
 __global__ void __launch_bounds__(kMidThreads) k_intermediate(const int32_t* P, int32_t* out,
                                                               int64_t n, int64_t ld,
-                                                              int64_t stride) {
-  extern __shared__ unsigned jw[];
+                                                              int64_t stride, int vec) {
+  extern __shared__ __align__(16) unsigned jw[];
   const int nn = (int)n, tid = threadIdx.x;
   const int64_t b = blockIdx.x / n;
   const int i = (int)(blockIdx.x % n);
   const int64_t off = b * stride + (int64_t)i * ld;
-  // ancestor = the last hop (none: the source, unreachable vertices, entries
-  // outside [0, n)); nothing strictly between a vertex and its last hop
-  for (int v = tid; v < nn; v += kMidThreads) {
-    const int p = P[off + v];
-    const bool tree = v != i && p >= 0 && p < nn && p != v;
-    jw[v] = mid_word(tree ? (unsigned)p : kNone, 0u);
+  const int nv = vec ? nn & ~3 : 0;
+#pragma unroll 4
+  for (int q = 4 * tid; q < nv; q += 4 * kMidThreads) {
+    const int4 p4 = *reinterpret_cast<const int4*>(P + off + q);
+    uint4 w4;
+    w4.x = mid_init(q, p4.x, i, nn);
+    w4.y = mid_init(q + 1, p4.y, i, nn);
+    w4.z = mid_init(q + 2, p4.z, i, nn);
+    w4.w = mid_init(q + 3, p4.w, i, nn);
+    *reinterpret_cast<uint4*>(jw + q) = w4;
   }
+  for (int v = nv + tid; v < nn; v += kMidThreads) jw[v] = mid_init(v, P[off + v], i, nn);
   __syncthreads();
   // jump until every ancestor is the source (whose word has no ancestor):
   // word v = (a, t) becomes (ancestor of a, max(t, a + 1, t of a)).  Every
   // word is one 32-bit access, so a thread combines a consistent pair even
-  // while others advance within the same round; the round cap stops a pred
-  // with a cycle (its vertices never reach the source and are written -1).
+  // while others (or its own earlier stores) advance within the same round;
+  // each thread reads four words and their ancestors' words before it writes
+  // any, so the shared-memory round trips overlap.  The round cap stops a
+  // pred with a cycle (its vertices never reach the source and are written
+  // -1).
   for (int round = 0; (1 << round) <= 2 * nn; ++round) {
     bool moved = false;
-    for (int v = tid; v < nn; v += kMidThreads) {
-      const unsigned w = jw[v], a = mid_anc(w);
-      if (a == kNone) continue;
-      const unsigned wa = jw[a], aa = mid_anc(wa);
-      if (aa == kNone) continue;
-      jw[v] = mid_word(aa, max(max(mid_top1(w), a + 1u), mid_top1(wa)));
-      moved = true;
+    for (int v0 = tid; v0 < nn; v0 += 4 * kMidThreads) {
+      unsigned w[4], wa[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int v = v0 + u * kMidThreads;
+        w[u] = v < nn ? jw[v] : mid_word(kNone, 0u);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const unsigned a = mid_anc(w[u]);
+        wa[u] = a != kNone ? jw[a] : mid_word(kNone, 0u);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const unsigned a = mid_anc(w[u]), aa = mid_anc(wa[u]);
+        if (a != kNone && aa != kNone) {
+          jw[v0 + u * kMidThreads] =
+              mid_word(aa, max(max(mid_top1(w[u]), a + 1u), mid_top1(wa[u])));
+          moved = true;
+        }
+      }
     }
     if (!__syncthreads_or(moved)) break;
   }
   // the row's reads all precede these writes (the barrier above), so out may
   // be pred itself
-  for (int v = tid; v < nn; v += kMidThreads) {
-    const unsigned w = jw[v];
-    out[off + v] = mid_anc(w) == (unsigned)i ? (int32_t)mid_top1(w) - 1 : -1;
+#pragma unroll 4
+  for (int q = 4 * tid; q < nv; q += 4 * kMidThreads) {
+    const uint4 w4 = *reinterpret_cast<const uint4*>(jw + q);
+    const int4 o = make_int4(mid_out(w4.x, i), mid_out(w4.y, i), mid_out(w4.z, i),
+                             mid_out(w4.w, i));
+    *reinterpret_cast<int4*>(out + off + q) = o;
   }
+  for (int v = nv + tid; v < nn; v += kMidThreads) out[off + v] = mid_out(jw[v], i);
 }
 
 }  // namespace
@@ -135,8 +177,10 @@ extern "C" fw_status fw_intermediate(const int32_t* pred, int32_t* out, int64_t 
                    kMidThreads) < 1)
     return FW_ERR_CUDA;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  k_intermediate<<<(unsigned)(batch * n), kMidThreads, smem, s>>>(pred, out, n, ld,
-                                                                   batch > 1 ? stride : 0);
+  const bool vec = ((uintptr_t)pred % 16) == 0 && ((uintptr_t)out % 16) == 0 && ld % 4 == 0 &&
+                   (batch <= 1 || stride % 4 == 0);
+  k_intermediate<<<(unsigned)(batch * n), kMidThreads, smem, s>>>(
+      pred, out, n, ld, batch > 1 ? stride : 0, vec ? 1 : 0);
   return cudaGetLastError() == cudaSuccess ? FW_OK : FW_ERR_CUDA;
 }
 
