@@ -120,6 +120,12 @@ typedef struct fw_options {
   int32_t trace_stride;
   int32_t tile_tma;           /* persistent driver: 1 (default) loads each remaining or panel
                                  tile with one 2-D TMA tensor copy, 0 = one bulk copy per row */
+  uint64_t debug_shuffle;     /* batched plans: nonzero = a seed; the plan's claim order is
+                                 permuted at random inside each wave segment (one phase of one
+                                 round of every graph: tasks none of which depends on another),
+                                 a stress of the dependency protocol under other orders of the
+                                 same tasks; 0 = off (the planned order).  Single solves ignore
+                                 it (their queue order is computed on the device) */
 } fw_options;
 
 /* Fills *opt with the defaults used by fw_solve. */
@@ -206,6 +212,20 @@ fw_status fw_batched_plan_info(const fw_batched_plan* plan, int32_t* bs_per_grap
                                int64_t* total_tasks);
 
 fw_status fw_batched_plan_destroy(fw_batched_plan* plan);
+
+/*
+ * fw_batched_task_list: diagnostic view of the claim order a batched plan
+ * uses for `batch` graphs of n[b] vertices and block sizes bs[b] (32, 64 or
+ * 128) on a GPU with `sms` CTAs, with opt->debug_shuffle applied (opt NULL:
+ * defaults, no shuffle).  Writes two int32 per task -- the graph, and the
+ * task's index in that graph's queue as fw_queue_tasks numbers it -- for all
+ * sum_b ceil(n[b] / bs[b])^3 tasks; *count gets that total.  Host only.
+ * FW_ERR_ARG for a NULL pointer, batch outside [1, 65536], sms < 1, an n
+ * outside [1, 131072], another block size, or cap (rows of out) below the
+ * total; FW_ERR_UNSUPPORTED when a graph would have over 1024 rounds.
+ */
+fw_status fw_batched_task_list(const int64_t* n, const int32_t* bs, int64_t batch, int32_t sms,
+                               const fw_options* opt, int32_t* out, int64_t cap, int64_t* count);
 
 /*
  * Block-size table of the batched planner for element type dtype (FW_I32 or

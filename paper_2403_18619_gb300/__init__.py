@@ -18,7 +18,7 @@ __all__ = [
     "FWError", "Options", "load", "check", "fw_solve", "fw_solve_ex", "fw_solve_host",
     "fw_solve_host_io", "fw_solve_noalloc", "fw_sync_status", "fw_backward", "fw_backward_strided",
     "fw_peak_probe", "fw_verify_certificate", "fw_release_workspace", "fw_solve_plan",
-    "fw_queue_tasks", "fw_paths", "fw_intermediate", "fw_tile_closure", "fw_tile_minplus", "fw_block_init_pred",
+    "fw_queue_tasks", "fw_batched_task_list", "fw_paths", "fw_intermediate", "fw_tile_closure", "fw_tile_minplus", "fw_block_init_pred",
     "BatchedPlan", "fw_bs_table", "fw_autotune_bs", "padded", "solve",
     "solve_batched", "INF_I32", "INF_I64", "FW_I32", "FW_F32", "FW_I64", "FW_F64", "DRIVER_AUTO",
     "DRIVER_PERSISTENT", "DRIVER_PHASED",
@@ -58,6 +58,7 @@ class Options(ctypes.Structure):
         ("trace_cap", ctypes.c_int64),
         ("trace_stride", ctypes.c_int32),
         ("tile_tma", ctypes.c_int32),
+        ("debug_shuffle", ctypes.c_uint64),
     ]
 
     @classmethod
@@ -105,6 +106,7 @@ def load():
         lib.fw_peak_probe.argtypes = [I32, P, P, P, P]
         lib.fw_verify_certificate.argtypes = [P, P, P, I64, I64, P, P]
         lib.fw_queue_tasks.argtypes = [I32, I64, I64, I64, P]
+        lib.fw_batched_task_list.argtypes = [P, P, I64, I32, P, P, I64, P]
         lib.fw_solve_plan.argtypes = [I64, I32, P, I32, P, P, P, P]
         lib.fw_paths.argtypes = [P, I64, I64, P, P, I64, P, I64, P, P]
         lib.fw_intermediate.argtypes = [P, P, I64, I64, I64, I64, P]
@@ -121,7 +123,8 @@ def load():
                      "fw_solve_batched", "fw_batched_plan_info", "fw_batched_plan_destroy",
                      "fw_backward", "fw_backward_strided", "fw_sync_status",
                      "fw_release_workspace", "fw_peak_probe", "fw_verify_certificate",
-                     "fw_queue_tasks", "fw_solve_noalloc", "fw_bs_table", "fw_autotune_bs",
+                     "fw_queue_tasks", "fw_batched_task_list", "fw_solve_noalloc", "fw_bs_table",
+                     "fw_autotune_bs",
                      "fw_solve_plan", "fw_paths", "fw_intermediate", "fw_tile_closure",
                      "fw_tile_minplus",
                      "fw_block_init_pred"):
@@ -371,6 +374,23 @@ def fw_queue_tasks(R: int, lookahead: int, first: int = 0, count: int | None = N
     out = np.zeros((count, 4), np.int32)
     check(load().fw_queue_tasks(R, lookahead, first, count, out.ctypes.data), "fw_queue_tasks")
     return out
+
+
+def fw_batched_task_list(ns, bss, sms: int = 152, options: Options | None = None) -> np.ndarray:
+    """The claim order of a batched plan of graphs with ns[b] vertices and
+    block sizes bss[b]: rows of (graph, task index in that graph's queue)."""
+    ns = np.ascontiguousarray(np.asarray(ns, np.int64))
+    bss = np.ascontiguousarray(np.asarray(bss, np.int32))
+    if ns.shape != bss.shape or ns.ndim != 1:
+        raise ValueError("ns and bss must be 1-D of equal length")
+    total = int(sum(-(-int(n) // int(b)) ** 3 for n, b in zip(ns, bss)))
+    out = np.zeros((max(total, 1), 2), np.int32)
+    cnt = ctypes.c_int64()
+    o = ctypes.byref(options) if options is not None else None
+    check(load().fw_batched_task_list(ns.ctypes.data, bss.ctypes.data, len(ns), sms, o,
+                                      out.ctypes.data, total, ctypes.byref(cnt)),
+          "fw_batched_task_list")
+    return out[:cnt.value]
 
 
 def _block(t, name):

@@ -344,6 +344,7 @@ void fw_options_default(fw_options* o) {
   o->trace_cap = 0;
   o->trace_stride = 0;
   o->tile_tma = 1;
+  o->debug_shuffle = 0;
 }
 
 const char* fw_status_string(fw_status s) {

@@ -137,6 +137,80 @@ int table_bs(int64_t n, fw_dtype dt) {
 constexpr size_t kAl = 256;
 size_t al(size_t x) { return (x + kAl - 1) / kAl * kAl; }
 
+// SplitMix64 (Steele, Lea and Flood, OOPSLA 2014): the debug shuffle's
+// random stream.
+uint64_t splitmix_next(uint64_t& x) {
+  uint64_t z = (x += 0x9e3779b97f4a7c15ull);
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  return z ^ (z >> 31);
+}
+
+// The global task list of `ns.size()` graphs with R[g] rounds each: (graph,
+// task index in that graph's queue), in claim order; look[g] and offs[g]
+// receive each graph's lookahead and queue stage offsets.  Stage waves, phase by phase: a graph's stage s is
+// [pivot(s)] [its first remaining tiles of round s-1] [panels(s)] [the rest
+// of round s-1] [round s's tiles in tile row / column s+1] (decode_task's
+// layout), and the wave emits segment 0 of every graph, then segment 1 of
+// every graph, ...  So the tiles between one graph's pivot and its panels
+// are every graph's (a pivot takes about as long as 3 remaining tiles, far
+// more than its own graph's tiles cover when many graphs share the GPU), and
+// each graph's own tasks keep their order: the list stays a topological
+// order of every graph's dependencies.
+//
+// shuffle != 0 permutes each wave segment (Fisher-Yates, seeded): a segment
+// holds one phase of one round of each graph -- pivots, remaining tiles of
+// one round, or panels of one round -- and no task of a segment depends on
+// another of the same segment, so every permutation is still a topological
+// order (a stress of the dependency protocol under other claim orders).
+fw_status build_task_list(const std::vector<int64_t>& ns, const std::vector<int>& R, int sms,
+                          uint64_t shuffle, std::vector<uint2>& list, std::vector<int64_t>& look,
+                          std::vector<std::vector<unsigned>>& offs) {
+  const int64_t B = (int64_t)ns.size();
+  std::vector<int64_t> order(B);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int64_t x, int64_t y) { return ns[x] > ns[y]; });
+  offs.assign(B, {});
+  int maxR = 0;
+  int64_t total = 0;
+  look.assign(B, 0);
+  for (int64_t g = 0; g < B; ++g) {
+    look[g] = auto_lookahead(R[g], sms);
+    offs[g].resize(R[g] + 2);
+    fill_stage_offsets(R[g], look[g], offs[g].data());
+    maxR = std::max(maxR, R[g]);
+    total += (int64_t)R[g] * R[g] * R[g];
+  }
+  if (total >= (int64_t)1 << 31) return FW_ERR_UNSUPPORTED;
+  list.clear();
+  list.reserve(total);
+  uint64_t rng = shuffle;
+  for (int s = 0; s <= maxR; ++s)
+    for (int seg = 0; seg < 5; ++seg) {
+      const size_t wave0 = list.size();
+      for (int64_t oi = 0; oi < B; ++oi) {
+        const int64_t g = order[oi];
+        const int Rg = R[g];
+        if (s > Rg) continue;
+        const int64_t np = s < Rg ? 2 * (int64_t)(Rg - 1) : 0;
+        const int64_t nrest = s >= 1 ? size_rest(Rg, s - 1) : 0;
+        const int64_t gl =
+            s >= 1 && s < Rg ? std::min<int64_t>(look[g], nrest) : (s == Rg ? nrest : 0);
+        const int64_t len[5] = {s < Rg ? 1 : 0, gl, np, s >= 1 && s < Rg ? nrest - gl : 0,
+                                s < Rg ? size_L(Rg, s) : 0};
+        int64_t first = offs[g][s];
+        for (int k = 0; k < seg; ++k) first += len[k];
+        for (int64_t t = first; t < first + len[seg]; ++t)
+          list.push_back(make_uint2((unsigned)g, (unsigned)t));
+      }
+      if (shuffle)
+        for (size_t k = list.size() - wave0; k > 1; --k)
+          std::swap(list[wave0 + k - 1], list[wave0 + splitmix_next(rng) % k]);
+    }
+  if ((int64_t)list.size() != total) return FW_ERR_CUDA;  // the segments cover every stage
+  return FW_OK;
+}
+
 }  // namespace
 
 }  // namespace fwh
@@ -200,49 +274,12 @@ fw_status plan_build(fw_batched_plan* p) {
     off += al(ws_bytes[g]);
   }
   // the global task list (stage waves, largest graphs first)
-  std::vector<int64_t> order(B);
-  std::iota(order.begin(), order.end(), 0);
-  std::stable_sort(order.begin(), order.end(), [&](int64_t x, int64_t y) { return p->n[x] > p->n[y]; });
-  std::vector<std::vector<unsigned>> offs(B);
-  int maxR = 0;
-  int64_t total = 0;
-  std::vector<int64_t> look(B);
-  for (int64_t g = 0; g < B; ++g) {
-    look[g] = auto_lookahead(p->R[g], num_sms());
-    offs[g].resize(p->R[g] + 2);
-    fill_stage_offsets(p->R[g], look[g], offs[g].data());
-    maxR = std::max(maxR, p->R[g]);
-    total += (int64_t)p->R[g] * p->R[g] * p->R[g];
-  }
-  if (total >= (int64_t)1 << 31) return FW_ERR_UNSUPPORTED;
   std::vector<uint2> list;
-  list.reserve(total);
-  // Stage waves, phase by phase: a graph's stage s is [pivot(s)] [its first
-  // remaining tiles of round s-1] [panels(s)] [the rest of round s-1]
-  // [round s's tiles in tile row / column s+1] (decode_task's layout), and the
-  // wave emits segment 0 of every graph, then segment 1 of every graph, ...
-  // So the tiles between one graph's pivot and its panels are every graph's
-  // (a pivot takes about as long as 3 remaining tiles, far more than its own
-  // graph's tiles cover when many graphs share the GPU), and each graph's own
-  // tasks keep their order: the list stays a topological order of every
-  // graph's dependencies.
-  for (int s = 0; s <= maxR; ++s)
-    for (int seg = 0; seg < 5; ++seg)
-      for (int64_t oi = 0; oi < B; ++oi) {
-        const int64_t g = order[oi];
-        const int R = p->R[g];
-        if (s > R) continue;
-        const int64_t np = s < R ? 2 * (int64_t)(R - 1) : 0;
-        const int64_t nrest = s >= 1 ? size_rest(R, s - 1) : 0;
-        const int64_t gl = s >= 1 && s < R ? std::min<int64_t>(look[g], nrest) : (s == R ? nrest : 0);
-        const int64_t len[5] = {s < R ? 1 : 0, gl, np, s >= 1 && s < R ? nrest - gl : 0,
-                                s < R ? size_L(R, s) : 0};
-        int64_t first = offs[g][s];
-        for (int k = 0; k < seg; ++k) first += len[k];
-        for (int64_t t = first; t < first + len[seg]; ++t)
-          list.push_back(make_uint2((unsigned)g, (unsigned)t));
-      }
-  if ((int64_t)list.size() != total) return FW_ERR_CUDA;  // the segments cover every stage
+  std::vector<int64_t> look;
+  std::vector<std::vector<unsigned>> offs;
+  const fw_status lst =
+      build_task_list(p->n, p->R, num_sms(), p->opt.debug_shuffle, list, look, offs);
+  if (lst != FW_OK) return lst;
   p->ntasks = (int64_t)list.size();
   const size_t list_off = off;
   off += al(list.size() * sizeof(uint2));
@@ -515,6 +552,36 @@ fw_status fw_batched_plan_create(fw_batched_plan** plan, const int64_t* n, const
     return st;
   }
   *plan = p;
+  return FW_OK;
+}
+
+fw_status fw_batched_task_list(const int64_t* n, const int32_t* bs, int64_t batch, int32_t sms,
+                               const fw_options* opt, int32_t* out, int64_t cap, int64_t* count) {
+  if (!n || !bs || !out || !count || batch < 1 || batch > 65536 || sms < 1 || cap < 0)
+    return FW_ERR_ARG;
+  fw_options o;
+  fw_options_default(&o);
+  if (opt) o = *opt;
+  std::vector<int64_t> ns(n, n + batch);
+  std::vector<int> R(batch);
+  for (int64_t g = 0; g < batch; ++g) {
+    if (ns[g] < 1 || ns[g] > 131072 || (bs[g] != 32 && bs[g] != 64 && bs[g] != 128))
+      return FW_ERR_ARG;
+    const int64_t r = (ns[g] + bs[g] - 1) / bs[g];
+    if (r > 1024) return FW_ERR_UNSUPPORTED;
+    R[g] = (int)r;
+  }
+  std::vector<uint2> list;
+  std::vector<int64_t> look;
+  std::vector<std::vector<unsigned>> offs;
+  const fw_status st = build_task_list(ns, R, sms, o.debug_shuffle, list, look, offs);
+  if (st != FW_OK) return st;
+  *count = (int64_t)list.size();
+  if (cap < *count) return FW_ERR_ARG;
+  for (size_t k = 0; k < list.size(); ++k) {
+    out[2 * k] = (int32_t)list[k].x;
+    out[2 * k + 1] = (int32_t)list[k].y;
+  }
   return FW_OK;
 }
 

@@ -124,6 +124,104 @@ def test_queue_is_complete_and_topological(fw, R, look):
             assert d < idx, (q[idx].tolist(), q[d].tolist())
 
 
+def _check_order(q, pos):
+    """Every dependency of the persistent engine precedes its task: q holds one
+    graph's queue rows (type, round, tile row, tile column) by task index, pos
+    the claim position of each task index.  Besides the queue's own rules, the
+    task of tile (r+1, r+1) in round r runs the pivot of round r+1 too, so it
+    also waits for that pivot's snapshot slot (the panels of round r-1) and
+    precedes round r+1's panels."""
+    at = {}
+    p2, p3 = {}, {}
+    for t, (typ, r, i, j) in enumerate(q.tolist()):
+        at[(r, i, j)] = pos[t]
+        if typ in (1, 2):
+            p2.setdefault(r, []).append(pos[t])
+        if typ == 3:
+            p3.setdefault(r, []).append(pos[t])
+    for t, (typ, r, i, j) in enumerate(q.tolist()):
+        deps = []
+        if r >= 1:
+            deps.append(at[(r - 1, i, j)])
+        if typ in (1, 2):
+            deps.append(at[(r, r, r)])
+            if r >= 1:
+                deps.append(at[(r - 1, r, r)])      # the fused task that closed the pivot
+        if typ == 3:
+            deps += [at[(r, i, r)], at[(r, r, j)]]
+        if typ == 0 and r >= 2:
+            deps += p2.get(r - 2, [])
+        if typ == 3 and i == j == r + 1 and r >= 1:
+            deps += p2.get(r - 1, [])               # the fused pivot's snapshot slot
+        if typ in (1, 2) and r >= 2:
+            deps += p3.get(r - 2, [])
+        for d in deps:
+            assert d < pos[t], (q[t].tolist(), d, pos[t])
+
+
+@pytest.mark.parametrize("seed", [0, 1, 7, 2 ** 63 + 5])
+def test_batched_task_list_orders(fw, seed):
+    """The batched plan's claim order (host only): every task of every graph
+    exactly once, each graph's dependencies in order -- with the planned
+    order (seed 0) and with the debug shuffle, which permutes each wave
+    segment (a different order for every seed, the same tasks)."""
+    ns = [700, 64, 300, 1000, 129, 33, 513]
+    bss = [64, 32, 32, 128, 64, 32, 128]
+    lst = fw.fw_batched_task_list(ns, bss, sms=152, options=fw.Options.default(debug_shuffle=seed))
+    Rs = [-(-n // b) for n, b in zip(ns, bss)]
+    assert len(lst) == sum(R ** 3 for R in Rs)
+    for g, (n, R) in enumerate(zip(ns, Rs)):
+        mine = np.flatnonzero(lst[:, 0] == g)
+        ts = lst[mine, 1]
+        assert sorted(ts.tolist()) == list(range(R ** 3))
+        look = fw.fw_solve_plan(n, fw.Options.default(bs=bss[g]), sms=152)["lookahead"]
+        q = fw.fw_queue_tasks(R, look)
+        pos = np.empty(R ** 3, np.int64)
+        pos[ts] = mine
+        _check_order(q, pos)
+    plain = fw.fw_batched_task_list(ns, bss, sms=152)
+    # the checker fails a planted mistake: graph 3's first panel claimed
+    # before its pivot
+    R3 = Rs[3]
+    q3 = fw.fw_queue_tasks(R3, fw.fw_solve_plan(ns[3], fw.Options.default(bs=bss[3]),
+                                                sms=152)["lookahead"])
+    mine = np.flatnonzero(plain[:, 0] == 3)
+    pos = np.empty(R3 ** 3, np.int64)
+    pos[plain[mine, 1]] = mine
+    piv = int(np.flatnonzero((q3[:, 0] == 0) & (q3[:, 1] == 0))[0])
+    pan = int(np.flatnonzero((q3[:, 0] == 1) & (q3[:, 1] == 0))[0])
+    pos[piv], pos[pan] = pos[pan], pos[piv]
+    with pytest.raises(AssertionError):
+        _check_order(q3, pos)
+    if seed:
+        assert not np.array_equal(lst, plain)
+        other = fw.fw_batched_task_list(ns, bss, sms=152,
+                                        options=fw.Options.default(debug_shuffle=seed + 1))
+        assert not np.array_equal(lst, other)
+    else:
+        assert np.array_equal(lst, plain)
+
+
+def test_batched_task_list_checks(fw):
+    lib = fw.load()
+    import ctypes as C
+    ns = np.array([100, 40], np.int64)
+    bs = np.array([32, 64], np.int32)
+    out = np.zeros((64 + 1, 2), np.int32)
+    cnt = C.c_int64()
+    assert lib.fw_batched_task_list(ns.ctypes.data, bs.ctypes.data, 2, 152, None,
+                                    out.ctypes.data, 65, C.byref(cnt)) == 0 and cnt.value == 65
+    assert lib.fw_batched_task_list(ns.ctypes.data, bs.ctypes.data, 2, 152, None,
+                                    out.ctypes.data, 64, C.byref(cnt)) == 1    # cap too small
+    bad = np.array([32, 48], np.int32)
+    assert lib.fw_batched_task_list(ns.ctypes.data, bad.ctypes.data, 2, 152, None,
+                                    out.ctypes.data, 65, C.byref(cnt)) == 1
+    assert lib.fw_batched_task_list(ns.ctypes.data, bs.ctypes.data, 2, 0, None,
+                                    out.ctypes.data, 65, C.byref(cnt)) == 1    # sms < 1
+    assert lib.fw_batched_task_list(None, bs.ctypes.data, 2, 152, None,
+                                    out.ctypes.data, 65, C.byref(cnt)) == 1
+
+
 def test_batched_host_checks(fw):
     lib = fw.load()
     import ctypes as C

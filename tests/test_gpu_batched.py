@@ -59,6 +59,25 @@ def test_batched_int_mixed_sizes(bs):
         check_int_full(W, D, P, Do, Po, oracle.path_count_i64(W, Do))
 
 
+@pytest.mark.parametrize("seed", [3, 11])
+def test_batched_shuffled_claim_order(seed):
+    """The debug shuffle claims every wave segment's tasks in a random order
+    (int32 and fp32 graphs of mixed sizes and block sizes): the dependency
+    flags alone keep the results equal to the oracle's."""
+    m = fw()
+    Ws = _int_batch(20 + seed, 16, 20, 700, p=0.4)
+    out, _, _ = _run(Ws, m.Options.default(debug_shuffle=seed))
+    for W, (D, P) in zip(Ws, out):
+        Do, Po = oracle.fw_i64(W)
+        check_int_full(W, D, P, Do, Po, oracle.path_count_i64(W, Do))
+    ns = graphgen.batch_sizes(30 + seed, 8, 20, 400)
+    Wf = [graphgen.dense_graph_f32(int(n), seed=300 + b, p=0.5) for b, n in enumerate(ns)]
+    out, _, _ = _run(Wf, m.Options.default(debug_shuffle=seed))
+    for W, (D, P) in zip(Wf, out):
+        Do, Po = oracle.fw_f64(W)
+        check_f32(W, D, P, Do, Po)
+
+
 def test_batched_replay_and_new_buffers():
     Ws = _int_batch(5, 12, 30, 200, p=0.5)
     out, _, _ = _run(Ws, reps=3)          # recorded once, replayed twice
