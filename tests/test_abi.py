@@ -50,6 +50,24 @@ def test_status_strings_and_defaults(fw):
     assert o.tile_tma == 1
 
 
+def test_options_mirror_matches_header(fw, tmp_path):
+    """The binding's ctypes mirror of fw_options has the header's size and
+    field offsets (a C program compiled against include/fw.h prints them)."""
+    fields = [f for f, _ in fw.Options._fields_]
+    src = tmp_path / "layout.c"
+    src.write_text("#include <stdio.h>\n#include <stddef.h>\n#include \"fw.h\"\n"
+                   "int main(void) {\n  printf(\"%zu\\n\", sizeof(fw_options));\n" +
+                   "".join("  printf(\"%%zu\\n\", offsetof(fw_options, %s));\n" % f
+                           for f in fields) + "  return 0;\n}\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True, capture_output=True)
+    got = [int(x) for x in subprocess.run([str(exe)], check=True, capture_output=True,
+                                          text=True).stdout.split()]
+    assert got[0] == ctypes.sizeof(fw.Options)
+    assert got[1:] == [getattr(fw.Options, f).offset for f in fields]
+
+
 def test_host_argument_checks(fw):
     lib = fw.load()
     good = 0x10000  # never dereferenced: every call below fails its host-side checks
