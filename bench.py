@@ -40,10 +40,10 @@ BS = 128
 SAMPLE_N = 2048          # CPU baseline: leading 2048-vertex induced subgraph
 # DRAM bytes (read + write) of one k_persistent_ws launch of the current
 # kernel, keyed by (n, BS, driver); null in the line where no capture exists.
-# n = 32768: one ncu capture of the same kernel at n = 16384 (342.1e9 B)
+# n = 32768: one ncu capture of the same kernel at n = 16384 (339.4e9 B)
 # scaled by n^3; an upper bound, since the bytes above the algorithmic
 # 8 n^3 / BS (2.20e12 B here) are scattered predecessor stores whose share
-# falls as n grows (1.31x at n = 8192, 1.24x at n = 16384).
+# falls as n grows (1.29x at n = 8192, 1.23x at n = 16384).
 TRAFFIC_BYTES = {(32768, 128, 1): 339.4e9 * 8}
 TRAFFIC_NOTE = {(32768, 128, 1): "ncu dram bytes of one launch at n = 16384, scaled by n^3 "
                                  "(upper bound; algorithmic 8 n^3 / BS = 2.20e12 B)"}
