@@ -9,8 +9,8 @@ relaxations.  The metric is relaxations per second, n^3 / t.
 
 Prints one JSON line.  `value` times the solve with the input already in HBM
 (the input is restored from a pristine device copy before every step, outside
-the timed events); `e2e` times fw_solve_host on pinned host buffers, copies
-included.  `roofline` compares the persistent solver kernel against the
+the timed events); `e2e` times fw_solve_host_io (the weights from one pinned
+host buffer, the results into others), copies included.  `roofline` compares the persistent solver kernel against the
 min-plus relaxation peak measured by fw_peak_probe in the same process.  The
 CPU baseline is the oracle's plain triple loop on a bounded sample of the same
 workload.  With --impl reference the oracle alone is timed the same way.
