@@ -203,7 +203,11 @@ fw_status fw_batched_plan_create(fw_batched_plan** plan, const int64_t* n, const
                                  int64_t batch, fw_dtype dtype, const fw_options* opt);
 
 /* dist[b], pred[b]: HOST arrays of device pointers (batch entries each); pred
- * NULL (or a NULL entry) solves for distances only. */
+ * NULL (or a NULL entry) solves for distances only.  A plan has one workspace
+ * and one recorded launch sequence, so its solves must not overlap on the
+ * GPU: issue them on one stream (stream order keeps them apart), or let the
+ * previous solve finish (e.g. synchronize its stream) before solving with the
+ * same plan on another stream.  Solves with different plans are independent. */
 fw_status fw_solve_batched(fw_batched_plan* plan, void* const* dist, int32_t* const* pred,
                            void* stream);
 

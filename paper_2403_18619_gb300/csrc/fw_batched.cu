@@ -415,7 +415,9 @@ fw_status solve_plan(fw_batched_plan* p, void* const* dist, int32_t* const* pred
   if (changed) {
     // New buffers: refresh the device table of per-graph arguments, which the
     // recorded kernels read when they run, with a copy ordered on s behind
-    // the previous solve.  Only a new status word (a solve on another stream)
+    // the previous solve (the caller keeps a plan's solves from overlapping:
+    // one stream, or the previous solve finished before another stream
+    // takes the plan).  Only a new status word (a solve on another stream)
     // changes a kernel parameter of the recorded graph and needs a new
     // recording, after that stream's earlier work.
     const bool restream = st != p->cur_status;
