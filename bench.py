@@ -659,7 +659,7 @@ def run_gpu(args):
         "vs_baseline": None,
         "dtype": "int32",
         "data": "synthetic",
-        "config": {"workload": workload_name(n), "n": n, "edge_p": P_EDGE, "weights": [LO, HI],
+        "config": {"workload": workload_name(n), "n": n, "seed": SEED, "edge_p": P_EDGE, "weights": [LO, HI],
                    "bs": args.bs, "driver": "phased" if args.driver == 2 else "persistent",
                    "parallelism": "replicas x%d" % world,
                    "l2": "no flush: %.1f GiB of dist+pred per step, far above the 129 MB L2"
