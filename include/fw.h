@@ -141,7 +141,7 @@ const char* fw_status_string(fw_status s);
  *         and the distances on exit.
  *   pred  device pointer, n x ld int32, output only (may not alias dist); NULL
  *         for a distance-only solve (no predecessor work at all; fp32 then
- *         relaxes with an add and a min per step instead of compare+select).
+ *         relaxes with an add and a min per step and keeps no argmin).
  *   n     vertices, 1 <= n <= 131072.   ld  leading dimension, ld >= n, ld % 4 == 0.
  *   dtype FW_I32, FW_F32, FW_I64 or FW_F64.
  * Returns FW_OK once the work is enqueued; FW_ERR_UNSUPPORTED for BS = 128
